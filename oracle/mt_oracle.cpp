@@ -1,0 +1,538 @@
+// FP64 CPU oracle of the null-geodesic ray tracer (arXiv 2111.08744, Sect. 2.2-2.5).
+//
+// TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the
+// benchmark's CPU-baseline leg may load this library; the product path (the
+// CUDA library and its Python binding) never does and shares no code with it.
+//
+// Plain, slow, obviously correct: every stage of every RK4 step re-derives the
+// cell indices from the position, looks each cell up by binary search in the
+// level's sorted key vector (the paper's sorted-vector octree, Sect. 3.1), and
+// evaluates the CIC weights of Eq. (8) corner by corner.  Compiled with
+// -ffp-contract=off so every operation is a single IEEE-754 double operation.
+//
+// Conventions (c = 1, lengths and eta in h^-1 Mpc, phi = Phi/c^2):
+//   * state y = (x[3], eta, k0, k[3], I, s), affine parameter lambda;
+//   * rays start at the observer with k0 = -1 (past-directed, so eta decreases
+//     while lambda increases; Eqs. (2)-(3) are invariant under k -> -k) and
+//     k^i = n sqrt((1 + 2 phi_o)/(1 - 2 phi_o)) (null condition of Eq. (1));
+//   * coarse cell coordinates u = x / dx_0 (IEEE division), wrapped into
+//     [0, N_c) by u - N_c floor(u / N_c) when periodic; level-l coordinates are
+//     u 2^l (exact);
+//   * a step uses h = dx_l / (N |k0|) with l the most refined level whose cell
+//     contains the photon at the step start (Sect. 2.2, "N steps per AMR cell");
+//   * the last step is shortened so that eta lands on eta_stop (iso-eta stop).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+extern "C" {
+
+struct orc_grid {
+  double box;
+  int32_t n_coarse;
+  int32_t n_levels;      // refined levels; level indices 0..n_levels
+  int32_t periodic;
+  int32_t n_slices;
+  const double* slice_eta;  // [n_slices], ascending
+};
+
+struct orc_level {
+  const uint64_t* keys;     // [count], ascending Morton keys (x bit 0, y bit 1, z bit 2)
+  const double* records;    // [count][n_slices][4]: phi, dphi/dx, dphi/dy, dphi/dz
+  int64_t count;
+};
+
+struct orc_params {
+  int32_t n_cones;
+  int32_t steps_per_cell;
+  int32_t gravity_on;
+  int32_t pad;
+  const double* observer;   // [n_cones][3]
+  const double* z_max;      // [n_cones]
+  const int64_t* ray_begin; // [n_cones + 1]
+  int64_t max_steps;
+};
+
+struct orc_out {
+  double* x;        // [3][N] end position (unwrapped)
+  double* k;        // [4][N] end k0, k1, k2, k3
+  double* eta;      // [N]
+  double* lambda;   // [N]
+  double* chi;      // [N] |x_s - x_o|
+  double* path;     // [N] integral of |k| d lambda
+  double* z0;       // [N] Eq. (23)
+  double* z1;       // [N] Eq. (24)
+  double* z4;       // [N] Eq. (27) with v = 0
+  double* z5;       // [N] Eq. (28) with v = 0
+  double* d_a;      // [N] a_s chi
+  double* d_l;      // [N] (1 + z5)^2 d_a
+  double* phi_o;    // [N]
+  double* phi_s;    // [N]
+  double* isw;      // [N] int phi_eta d eta from eta_s to eta_o
+  int32_t* n_steps; // [N]
+  int32_t* level;   // [N] most refined level containing the end point
+  int32_t* status;  // [N] 0 ok, 1 left domain, 2 max steps, 3 non-finite
+};
+
+}  // extern "C"
+
+namespace {
+
+enum { ST_OK = 0, ST_LEFT = 1, ST_MAXSTEPS = 2, ST_NONFINITE = 3 };
+
+uint64_t morton_key(int64_t i, int64_t j, int64_t k) {
+  uint64_t key = 0;
+  for (int b = 0; b < 21; ++b) {
+    key |= ((uint64_t)((i >> b) & 1)) << (3 * b);
+    key |= ((uint64_t)((j >> b) & 1)) << (3 * b + 1);
+    key |= ((uint64_t)((k >> b) & 1)) << (3 * b + 2);
+  }
+  return key;
+}
+
+// Background a(eta) and H(eta) = a'/a from the tabulated nodes (eta, a, H, dH/deta):
+// cubic Hermite interpolation with slopes a' = a H and H' (Sect. 2.2, "external
+// pre-computed tables").
+struct Background {
+  const double* tab;
+  int n;
+  int bracket(double eta) const {
+    // j with eta_j <= eta < eta_{j+1}, clamped to [0, n-2]
+    int lo = 0, hi = n - 1;
+    if (eta <= tab[0]) return 0;
+    if (eta >= tab[4 * (n - 1)]) return n - 2;
+    while (hi - lo > 1) {
+      int mid = (lo + hi) / 2;
+      if (tab[4 * mid] <= eta) lo = mid; else hi = mid;
+    }
+    return lo;
+  }
+  void eval(double eta, double* a, double* H) const {
+    int j = bracket(eta);
+    const double* p = tab + 4 * j;
+    const double* q = p + 4;
+    double d = q[0] - p[0];
+    double t = (eta - p[0]) / d;
+    double t2 = t * t, t3 = t2 * t;
+    double h00 = 2.0 * t3 - 3.0 * t2 + 1.0;
+    double h10 = t3 - 2.0 * t2 + t;
+    double h01 = -2.0 * t3 + 3.0 * t2;
+    double h11 = t3 - t2;
+    if (a) *a = h00 * p[1] + h10 * d * (p[1] * p[2]) + h01 * q[1] + h11 * d * (q[1] * q[2]);
+    if (H) *H = h00 * p[2] + h10 * d * p[3] + h01 * q[2] + h11 * d * q[3];
+  }
+  double a_of(double eta) const { double a; eval(eta, &a, nullptr); return a; }
+  // eta at which a(eta) = 1/(1+z), by bisection on the interpolant (monotone in eta)
+  double eta_stop(double z) const {
+    double target = 1.0 / (1.0 + z);
+    double lo = tab[0], hi = tab[4 * (n - 1)];
+    if (target >= a_of(hi)) return hi;
+    for (int it = 0; it < 200; ++it) {
+      double mid = 0.5 * (lo + hi);
+      if (mid == lo || mid == hi) break;
+      if (a_of(mid) < target) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+  }
+};
+
+struct Field {
+  double box;
+  int nc, L, S;
+  bool periodic;
+  const double* seta;
+  const orc_level* lv;
+
+  int64_t n_at(int l) const { return (int64_t)nc << l; }
+  double dx(int l) const { return box / (double)n_at(l); }
+
+  // coarse-unit coordinates of x (wrapped when periodic)
+  void coarse_coords(const double* x, double* u) const {
+    for (int d = 0; d < 3; ++d) {
+      double v = x[d] / dx(0);
+      if (periodic) v = v - (double)nc * std::floor(v / (double)nc);
+      u[d] = v;
+    }
+  }
+  // row of cell (i, j, k) at level l, or -1 when absent (binary search, Sect. 3.1)
+  int64_t find(int l, int64_t i, int64_t j, int64_t k) const {
+    int64_t n = n_at(l);
+    if (periodic) {
+      i = ((i % n) + n) % n; j = ((j % n) + n) % n; k = ((k % n) + n) % n;
+    } else if (i < 0 || j < 0 || k < 0 || i >= n || j >= n || k >= n) {
+      return -1;
+    }
+    uint64_t key = morton_key(i, j, k);
+    const uint64_t* b = lv[l].keys;
+    const uint64_t* e = b + lv[l].count;
+    const uint64_t* p = std::lower_bound(b, e, key);
+    if (p == e || *p != key) return -1;
+    return (int64_t)(p - b);
+  }
+  // most refined level whose cell contains the point (-1: outside the domain)
+  int finest(const double* u) const {
+    int best = -1;
+    for (int l = 0; l <= L; ++l) {
+      double s = std::ldexp(1.0, l);
+      int64_t c[3];
+      for (int d = 0; d < 3; ++d) c[d] = (int64_t)std::floor(u[d] * s);
+      if (find(l, c[0], c[1], c[2]) < 0) break;
+      best = l;
+    }
+    return best;
+  }
+  // CIC (Eq. 8) of the 4 record components at slice s, level l; false when a neighbour is absent.
+  bool cic_level(int l, const double* u, double (*vals)[4]) const {
+    double s = std::ldexp(1.0, l);
+    double U[3];
+    int64_t i0[3];
+    for (int d = 0; d < 3; ++d) {
+      U[d] = u[d] * s;
+      i0[d] = (int64_t)std::floor(U[d] - 0.5);
+    }
+    int64_t rows[8];
+    for (int c = 0; c < 8; ++c) {
+      rows[c] = find(l, i0[0] + (c & 1), i0[1] + ((c >> 1) & 1), i0[2] + ((c >> 2) & 1));
+      if (rows[c] < 0) return false;
+    }
+    for (int sl = 0; sl < S; ++sl)
+      for (int q = 0; q < 4; ++q) vals[sl][q] = 0.0;
+    for (int c = 0; c < 8; ++c) {
+      double w = 1.0;
+      for (int d = 0; d < 3; ++d) {
+        double centre = (double)(i0[d] + ((c >> d) & 1)) + 0.5;
+        double r = U[d] - centre;
+        w = w * (1.0 - std::fabs(r));   // W_CIC(r) = 1 - |r| for |r| < 1
+      }
+      const double* rec = lv[l].records + (size_t)rows[c] * (size_t)S * 4;
+      for (int sl = 0; sl < S; ++sl)
+        for (int q = 0; q < 4; ++q) vals[sl][q] += w * rec[sl * 4 + q];
+    }
+    return true;
+  }
+  // Interpolated phi, grad phi and d phi/d eta at (u, eta), with the level fallback of
+  // Sect. 2.2 (start at the most refined level containing the photon, go coarser while a
+  // neighbour is missing).  Time: linear in eta between the bracketing slices.
+  // Returns false when even level 0 lacks neighbours (edge of a non-periodic domain).
+  bool sample(const double* u, double eta, double* phi, double* grad, double* phi_eta, int* lev_used) const {
+    int lf = finest(u);
+    if (lf < 0) return false;
+    double vals[64][4];
+    int l = lf;
+    for (; l >= 0; --l)
+      if (cic_level(l, u, vals)) break;
+    if (l < 0) return false;
+    if (lev_used) *lev_used = l;
+    if (S == 1) {
+      *phi = vals[0][0];
+      for (int d = 0; d < 3; ++d) grad[d] = vals[0][1 + d];
+      *phi_eta = 0.0;
+      return true;
+    }
+    int s = 0;
+    while (s < S - 2 && seta[s + 1] <= eta) ++s;
+    double de = seta[s + 1] - seta[s];
+    double w = (eta - seta[s]) / de;   // linear in eta; outside the slices: extended linearly
+    *phi = vals[s][0] + w * (vals[s + 1][0] - vals[s][0]);
+    for (int d = 0; d < 3; ++d) grad[d] = vals[s][1 + d] + w * (vals[s + 1][1 + d] - vals[s][1 + d]);
+    *phi_eta = (vals[s + 1][0] - vals[s][0]) / de;
+    return true;
+  }
+};
+
+struct Tracer {
+  Field f;
+  Background bg;
+  int N;          // steps per cell
+  bool gravity;
+  int64_t max_steps;
+
+  // Right-hand side of Eqs. (2)-(3) with d phi/d lambda from the chain rule, Eq. (4).
+  bool rhs(const double* y, double* dy) const {
+    const double* x = y;
+    double eta = y[3], k0 = y[4];
+    const double* k = y + 5;
+    double a, H;
+    bg.eval(eta, &a, &H);
+    double phi = 0.0, g[3] = {0.0, 0.0, 0.0}, pe = 0.0;
+    if (gravity) {
+      double u[3];
+      f.coarse_coords(x, u);
+      if (!f.sample(u, eta, &phi, g, &pe, nullptr)) return false;
+    }
+    double dphidl = g[0] * k[0] + g[1] * k[1] + g[2] * k[2] + pe * k0;
+    dy[0] = k[0];
+    dy[1] = k[1];
+    dy[2] = k[2];
+    dy[3] = k0;
+    dy[4] = -2.0 * H * k0 * k0 - 2.0 * dphidl * k0 + 2.0 * pe * k0 * k0;
+    for (int i = 0; i < 3; ++i)
+      dy[5 + i] = -2.0 * H * k0 * k[i] + 2.0 * dphidl * k[i] - 2.0 * g[i] * k0 * k0;
+    dy[8] = -pe * k0;
+    dy[9] = std::sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+    return true;
+  }
+
+  struct Result {
+    double y[10];
+    double lambda, phi_o, phi_s;
+    int n_steps, level, status;
+  };
+
+  Result trace(const double* xo, const double* n, double eta_stop) const {
+    Result r;
+    double* y = r.y;
+    double eta_o = bg.tab[4 * (bg.n - 1)];
+    double phi_o = 0.0;
+    if (gravity) {
+      double u[3], g[3], pe;
+      f.coarse_coords(xo, u);
+      if (!f.sample(u, eta_o, &phi_o, g, &pe, nullptr)) phi_o = 0.0;
+    }
+    double kn = std::sqrt((1.0 + 2.0 * phi_o) / (1.0 - 2.0 * phi_o));
+    for (int d = 0; d < 3; ++d) y[d] = xo[d];
+    y[3] = eta_o;
+    y[4] = -1.0;
+    for (int d = 0; d < 3; ++d) y[5 + d] = n[d] * kn;
+    y[8] = 0.0;
+    y[9] = 0.0;
+    r.lambda = 0.0;
+    r.phi_o = phi_o;
+    r.n_steps = 0;
+    r.status = ST_OK;
+    if (!(y[3] > eta_stop)) goto done;
+    for (;;) {
+      if (r.n_steps >= max_steps) { r.status = ST_MAXSTEPS; break; }
+      double u[3];
+      f.coarse_coords(y, u);
+      int lf = f.finest(u);
+      if (lf < 0) { r.status = ST_LEFT; break; }
+      double k0 = y[4];
+      double h = f.dx(lf) / ((double)N * std::fabs(k0));
+      bool last = false;
+      if (y[3] + k0 * h <= eta_stop) { h = (eta_stop - y[3]) / k0; last = true; }
+      // classical RK4
+      double k1[10], k2[10], k3[10], k4[10], t[10];
+      if (!rhs(y, k1)) { r.status = ST_LEFT; break; }
+      for (int i = 0; i < 10; ++i) t[i] = y[i] + 0.5 * h * k1[i];
+      if (!rhs(t, k2)) { r.status = ST_LEFT; break; }
+      for (int i = 0; i < 10; ++i) t[i] = y[i] + 0.5 * h * k2[i];
+      if (!rhs(t, k3)) { r.status = ST_LEFT; break; }
+      for (int i = 0; i < 10; ++i) t[i] = y[i] + h * k3[i];
+      if (!rhs(t, k4)) { r.status = ST_LEFT; break; }
+      for (int i = 0; i < 10; ++i) y[i] = y[i] + (h / 6.0) * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+      r.lambda += h;
+      r.n_steps += 1;
+      bool finite = true;
+      for (int i = 0; i < 10; ++i) finite = finite && std::isfinite(y[i]);
+      if (!finite) { r.status = ST_NONFINITE; break; }
+      if (last) break;
+    }
+  done:
+    r.phi_s = 0.0;
+    r.level = -1;
+    {
+      double u[3];
+      f.coarse_coords(y, u);
+      r.level = f.finest(u);
+      if (gravity && r.status != ST_NONFINITE) {
+        double g[3], pe;
+        if (!f.sample(u, y[3], &r.phi_s, g, &pe, nullptr)) r.phi_s = 0.0;
+      }
+    }
+    return r;
+  }
+};
+
+Tracer make_tracer(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n, const orc_params* p) {
+  Tracer t;
+  t.f.box = g->box;
+  t.f.nc = g->n_coarse;
+  t.f.L = g->n_levels;
+  t.f.S = g->n_slices;
+  t.f.periodic = g->periodic != 0;
+  t.f.seta = g->slice_eta;
+  t.f.lv = lv;
+  t.bg.tab = bg;
+  t.bg.n = bg_n;
+  t.N = p->steps_per_cell;
+  t.gravity = p->gravity_on != 0;
+  t.max_steps = p->max_steps;
+  return t;
+}
+
+int cone_of(const orc_params* p, int64_t i) {
+  int c = 0;
+  while (c + 1 < p->n_cones && p->ray_begin[c + 1] <= i) ++c;
+  return c;
+}
+
+template <class F>
+void parallel_for(int64_t n, int n_threads, F fn) {
+  if (n_threads <= 1) { for (int64_t i = 0; i < n; ++i) fn(i); return; }
+  std::atomic<int64_t> next(0);
+  std::vector<std::thread> th;
+  for (int t = 0; t < n_threads; ++t)
+    th.emplace_back([&]() {
+      for (;;) {
+        int64_t i = next.fetch_add(1);
+        if (i >= n) break;
+        fn(i);
+      }
+    });
+  for (auto& x : th) x.join();
+}
+
+bool keys_sorted(const orc_grid* g, const orc_level* lv) {
+  for (int l = 0; l <= g->n_levels; ++l)
+    for (int64_t i = 1; i < lv[l].count; ++i)
+      if (!(lv[l].keys[i - 1] < lv[l].keys[i])) return false;
+  return true;
+}
+
+void xi_of(const double* y, double eta_stop, double* xi) {
+  // end point moved along the ray onto the iso-eta surface eta = eta_stop
+  for (int d = 0; d < 3; ++d) xi[d] = y[d] - (y[5 + d] / y[4]) * (y[3] - eta_stop);
+}
+
+}  // namespace
+
+extern "C" {
+
+double orc_eta_stop(const double* bg, int bg_n, double z) {
+  Background b{bg, bg_n};
+  return b.eta_stop(z);
+}
+
+void orc_background(const double* bg, int bg_n, const double* eta, int64_t n, double* a, double* H) {
+  Background b{bg, bg_n};
+  for (int64_t i = 0; i < n; ++i) b.eval(eta[i], a ? a + i : nullptr, H ? H + i : nullptr);
+}
+
+// Interpolated field at arbitrary points (tests of the lookup and of Eq. 8).
+int orc_sample(const orc_grid* g, const orc_level* lv, const double* pts /*[3][n]*/, const double* eta, int64_t n,
+               double* phi, double* grad /*[3][n]*/, double* phi_eta, int32_t* level_finest, int32_t* level_cic) {
+  if (!keys_sorted(g, lv)) return 4;
+  Field f;
+  f.box = g->box; f.nc = g->n_coarse; f.L = g->n_levels; f.S = g->n_slices;
+  f.periodic = g->periodic != 0; f.seta = g->slice_eta; f.lv = lv;
+  for (int64_t i = 0; i < n; ++i) {
+    double x[3] = {pts[i], pts[n + i], pts[2 * n + i]}, u[3], gr[3] = {0, 0, 0}, p = 0, pe = 0;
+    f.coarse_coords(x, u);
+    int lu = -1;
+    level_finest[i] = f.finest(u);
+    bool ok = f.sample(u, eta[i], &p, gr, &pe, &lu);
+    level_cic[i] = ok ? lu : -1;
+    phi[i] = p; phi_eta[i] = pe;
+    for (int d = 0; d < 3; ++d) grad[d * n + i] = gr[d];
+  }
+  return 0;
+}
+
+int orc_trace(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n, const orc_params* p,
+              const double* dirs /*[3][N]*/, int64_t n_rays, orc_out* o, int n_threads) {
+  if (!keys_sorted(g, lv)) return 4;
+  Tracer t = make_tracer(g, lv, bg, bg_n, p);
+  std::vector<double> es(p->n_cones);
+  for (int c = 0; c < p->n_cones; ++c) es[c] = t.bg.eta_stop(p->z_max[c]);
+  parallel_for(n_rays, n_threads, [&](int64_t i) {
+    int c = cone_of(p, i);
+    const double* xo = p->observer + 3 * c;
+    double n[3] = {dirs[i], dirs[n_rays + i], dirs[2 * n_rays + i]};
+    Tracer::Result r = t.trace(xo, n, es[c]);
+    const double* y = r.y;
+    double a_s = t.bg.a_of(y[3]);
+    double dxo[3] = {y[0] - xo[0], y[1] - xo[1], y[2] - xo[2]};
+    double chi = std::sqrt(dxo[0] * dxo[0] + dxo[1] * dxo[1] + dxo[2] * dxo[2]);
+    for (int d = 0; d < 3; ++d) o->x[d * n_rays + i] = y[d];
+    o->k[i] = y[4];
+    for (int d = 0; d < 3; ++d) o->k[(1 + d) * n_rays + i] = y[5 + d];
+    o->eta[i] = y[3];
+    o->lambda[i] = r.lambda;
+    o->chi[i] = chi;
+    o->path[i] = y[9];
+    double z0 = 1.0 / a_s - 1.0;                         // Eq. (23), a_0 = 1
+    double z1 = z0 + (r.phi_o - r.phi_s) / a_s;          // Eq. (24)
+    double z4 = z1 - 2.0 * y[8] / a_s;                   // Eq. (27), v = 0 so z3 = z2 = z1
+    // Eq. (28) with g_{mu nu} k^mu u^nu = -a k0 (1 + phi), v = 0, a_o = 1, k0_o = -1
+    double z5 = (a_s * std::fabs(y[4]) * (1.0 + r.phi_s)) / (1.0 * (1.0 + r.phi_o)) - 1.0;
+    o->z0[i] = z0; o->z1[i] = z1; o->z4[i] = z4; o->z5[i] = z5;
+    o->d_a[i] = a_s * chi;
+    o->d_l[i] = (1.0 + z5) * (1.0 + z5) * a_s * chi;
+    o->phi_o[i] = r.phi_o;
+    o->phi_s[i] = r.phi_s;
+    o->isw[i] = y[8];
+    o->n_steps[i] = r.n_steps;
+    o->level[i] = r.level;
+    o->status[i] = r.status;
+  });
+  return 0;
+}
+
+// Finite-beam distortion matrix, Eqs. (17)-(21): four rays at semi-aperture eps around
+// each central direction, all stopped on the iso-eta surface of the cone, end points
+// projected onto that surface, differences projected onto the screen (screen = 0:
+// the beta-screen orthogonal to the central ray's source direction; 1: the Sachs screen
+// orthogonal to the central ray's wave vector at the end).  Column 2 is taken as
+// (xi_D - xi_C) so that A reduces to the identity when phi = 0.
+int orc_bundle(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n, const orc_params* p,
+               const double* dirs, int64_t n_rays, double eps, int screen, double* A /*[4][N]*/, int n_threads) {
+  if (!keys_sorted(g, lv)) return 4;
+  Tracer t = make_tracer(g, lv, bg, bg_n, p);
+  std::vector<double> es(p->n_cones);
+  for (int c = 0; c < p->n_cones; ++c) es[c] = t.bg.eta_stop(p->z_max[c]);
+  parallel_for(n_rays, n_threads, [&](int64_t i) {
+    int c = cone_of(p, i);
+    const double* xo = p->observer + 3 * c;
+    double r[3] = {dirs[i], dirs[n_rays + i], dirs[2 * n_rays + i]};
+    double th1 = std::atan2(r[1], r[0]);
+    double th2 = std::acos(std::max(-1.0, std::min(1.0, r[2])));
+    double e1[3] = {-std::sin(th1), std::cos(th1), 0.0};
+    double e2[3] = {-std::cos(th1) * std::cos(th2), -std::sin(th1) * std::cos(th2), std::sin(th2)};
+    double te = std::tan(eps);
+    double dir[4][3];
+    double sgn[4] = {+1.0, -1.0, -1.0, +1.0};  // A, B, C, D
+    for (int b = 0; b < 4; ++b) {
+      const double* e = b < 2 ? e1 : e2;
+      double nn = 0.0;
+      for (int d = 0; d < 3; ++d) { dir[b][d] = r[d] + sgn[b] * te * e[d]; nn += dir[b][d] * dir[b][d]; }
+      nn = std::sqrt(nn);
+      for (int d = 0; d < 3; ++d) dir[b][d] /= nn;
+    }
+    Tracer::Result ref = t.trace(xo, r, es[c]);
+    double xr[3];
+    xi_of(ref.y, es[c], xr);
+    double xi[4][3];
+    for (int b = 0; b < 4; ++b) {
+      Tracer::Result rb = t.trace(xo, dir[b], es[c]);
+      xi_of(rb.y, es[c], xi[b]);
+    }
+    double v[3];
+    if (screen == 0) {
+      for (int d = 0; d < 3; ++d) v[d] = xr[d] - xo[d];
+    } else {
+      for (int d = 0; d < 3; ++d) v[d] = ref.y[5 + d];
+    }
+    double vn = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double b1 = std::atan2(v[1], v[0]);
+    double b2 = std::acos(std::max(-1.0, std::min(1.0, v[2] / vn)));
+    double s1[3] = {-std::sin(b1), std::cos(b1), 0.0};
+    double s2[3] = {-std::cos(b1) * std::cos(b2), -std::sin(b1) * std::cos(b2), std::sin(b2)};
+    double chi0 = std::sqrt((xr[0] - xo[0]) * (xr[0] - xo[0]) + (xr[1] - xo[1]) * (xr[1] - xo[1]) +
+                            (xr[2] - xo[2]) * (xr[2] - xo[2]));
+    double dAB[3], dDC[3];
+    for (int d = 0; d < 3; ++d) { dAB[d] = xi[0][d] - xi[1][d]; dDC[d] = xi[3][d] - xi[2][d]; }
+    double den = 2.0 * chi0 * te;
+    A[0 * n_rays + i] = (dAB[0] * s1[0] + dAB[1] * s1[1] + dAB[2] * s1[2]) / den;  // A11
+    A[1 * n_rays + i] = (dDC[0] * s1[0] + dDC[1] * s1[1] + dDC[2] * s1[2]) / den;  // A12
+    A[2 * n_rays + i] = (dAB[0] * s2[0] + dAB[1] * s2[1] + dAB[2] * s2[2]) / den;  // A21
+    A[3 * n_rays + i] = (dDC[0] * s2[0] + dDC[1] * s2[1] + dDC[2] * s2[2]) / den;  // A22
+  });
+  return 0;
+}
+
+}  // extern "C"
