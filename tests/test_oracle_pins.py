@@ -394,4 +394,8 @@ def test_step_size_follows_refinement_level():
     chi = o0["chi"]
     assert np.abs(o0["n_steps"] - 4 * chi / (box / n)).max() <= 1
     assert np.abs(o2["n_steps"] - 16 * chi / (box / n)).max() <= 1
-    np.testing.assert_allclose(o2["chi"], o0["chi"], rtol=1e-12)
+    # the end points, moved onto the iso-eta surface, agree (FLRW: straight rays)
+    es = oracle.eta_stop(w0.bg, 0.3)
+    d0 = np.linalg.norm(oracle.xi_on_surface(o0, es) - w0.observer[0][:, None], axis=0)
+    d2 = np.linalg.norm(oracle.xi_on_surface(o2, es) - w0.observer[0][:, None], axis=0)
+    np.testing.assert_allclose(d2, d0, rtol=1e-11)
