@@ -1,0 +1,288 @@
+"""Benchmark: rays/s to z = 1 through an AMR potential on one GB300 (or N replicas).
+
+Workload (synthetic, seeded): 256^3 coarse grid in a 1 h^-1 Gpc box plus 3 refinement
+levels (2%, 0.5%, 0.125% of the volume) on the densest cells, FP32 phi/grad phi records,
+two time slices (z = 0, 1) linear in eta, 786,432 HEALPix (nside 256, NESTED) rays from
+the box centre to z = 1, 4 RK4 steps per AMR cell, FP64 ray state.
+
+One timed step = one mt_trace_rays call over all rays (the whole hot path: locate, CIC
+with level fallback, geodesic RHS, RK4, stop, outputs).  The field (1.2 GB) is larger
+than L2, and L2 is also flushed between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reported CPU baseline) on a bounded
+sample of the same rays on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RK4 geodesic steps/s and rays/s to z=1 on AMR field; % of HBM roofline"
+UNIT = "rays/s"
+FIELD_BYTES_PER_STEP = 4 * 8 * 16 * 2   # 4 stages x 8 CIC records x 16 B (float4) x 2 bracketing slices
+
+
+def workload_config(w):
+    cells = [int(l.keys.size) for l in w.levels]
+    return {"workload": "AMR 256^3 + 3 levels, 786,432 rays to z=1 (mixed: FP32 field, FP64 state)",
+            "box_h-1Mpc": w.box, "n_coarse": w.n_coarse, "n_levels": w.n_levels, "cells_per_level": cells,
+            "n_slices": w.n_slices, "n_rays": w.n_rays, "z_max": float(w.z_max[0]),
+            "steps_per_cell": w.steps_per_cell, "field_precision": "fp32", "state_precision": "fp64",
+            "l2": "field 1.2 GB > L2; L2 flushed between timed steps"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(w, budget_s=15.0):
+    """Time the CPU oracle on a bounded, seeded sample of the rays; returns (rays/s, n, threads, secs)."""
+    import oracle
+    threads = oracle.default_threads()
+    rng = np.random.Generator(np.random.PCG64(2024))
+    n = 64
+    while True:
+        idx = np.sort(rng.choice(w.n_rays, size=n, replace=False))
+        t0 = time.perf_counter()
+        oracle.trace(w, dirs=w.dirs[:, idx], n_threads=threads)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or n >= w.n_rays:
+            return n / dt, n, threads, dt
+        n = min(w.n_rays, int(n * min(8.0, max(2.0, budget_s / max(dt, 1e-3) / 2))))
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2111_08744_gb300 import inputs as I
+    w = I.config_amr()
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, n, threads, dt = oracle_sample(w, budget_s=args.ref_budget)
+        if i >= args.warmup:
+            vals.append((v, n, dt))
+    value = float(np.mean([v for v, _, _ in vals]))
+    n = vals[-1][1]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean([d for _, _, d in vals]) * 1e3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.default_threads(),
+                             "kind": "oracle", "sample": f"{n} seeded rays of the 786,432 per step, FP64 field"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank):
+    import torch
+
+    from paper_2111_08744_gb300 import binding as B
+    from paper_2111_08744_gb300 import build as Bd
+    from paper_2111_08744_gb300 import inputs as I
+
+    Bd.build()
+    w = I.config_amr()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    levels32 = I.fp32_levels(w)
+    tree = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, levels32, w.bg, "fp32")
+    params = B.TraceParams.from_workload(w)
+    n = w.n_rays
+    dirs = torch.from_numpy(w.dirs).to(dev)
+    out = B.alloc_outputs(n, dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        B.trace_rays(tree, params, dirs, out)
+    torch.cuda.synchronize()
+    st = tree.device_status()
+    if st != B.MT_OK:
+        raise RuntimeError(f"device status after warm-up: {B.status_str(st)}")
+    total_steps = int(out["n_steps"].sum().item())
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        B.trace_rays(tree, params, dirs, out)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    wall = time.perf_counter() - wall0
+    ck = clocks.stop()
+    times = [a.elapsed_time(b) for a, b in ev]
+    ms = float(np.mean(times))
+    ms_max = max_over_ranks(ms, ws)
+    if int(out["n_steps"].sum().item()) != total_steps:
+        raise RuntimeError("step count changed between launches")
+    value = ws * n / (ms_max * 1e-3)
+    steps_per_s = ws * total_steps / (ms_max * 1e-3)
+
+    # end to end through the public API: host (pinned) directions in, host outputs back
+    host_dirs = torch.from_numpy(w.dirs).pin_memory()
+    host_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
+    h2d = host_dirs.numel() * 8
+    d2h = sum(v.numel() * v.element_size() for v in out.values())
+    e2e_ms = []
+    for i in range(max(1, min(args.steps, 3)) + 1):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        d = host_dirs.to(dev, non_blocking=True)
+        B.trace_rays(tree, params, d, out)
+        for k in out:
+            host_out[k].copy_(out[k], non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_value = ws * n / (max_over_ranks(float(np.mean(e2e_ms)), ws) * 1e-3)
+
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = FIELD_BYTES_PER_STEP * total_steps / (ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "traffic": None, "kernel": "trace_kernel<float>",
+            "algorithmic_bytes_per_rk4_step": FIELD_BYTES_PER_STEP, "rk4_steps_per_launch": total_steps,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, ns, threads, dt = oracle_sample(w, budget_s=args.ref_budget)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{ns} seeded rays of the 786,432 ({dt:.1f} s of FP64 oracle work on {threads} threads)"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 state / f32 field", "data": "synthetic", "config": workload_config(w),
+            "steps_per_s": steps_per_s, "rk4_steps_per_step": total_steps,
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": args.steps, "clocks": ck, "step_ms_all": times, "wall_s_timed": wall}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tree.free()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * mt.h -- C ABI of the GB300 null-geodesic ray tracer.
+ *
+ * The method is the one of Breton & Reverdy, arXiv 2111.08744
+ * ("Magrathea-Pathfinder"): photons are integrated backward from an observer
+ * on the null geodesics of the weakly perturbed FLRW metric (Eq. 1),
+ *     ds^2 = a^2(eta) [ -(1 + 2 phi) d eta^2 + (1 - 2 phi) dx^2 ],
+ * with the geodesic equations (Eqs. 2-3) and d phi / d lambda from the chain
+ * rule (Eq. 4), by classical RK4 in the affine parameter with N steps per
+ * AMR cell (Sect. 2.2); phi and grad phi are CIC-interpolated (Eq. 8) from an
+ * octree with the level fallback of Sect. 2.2 / Fig. 1; per ray the library
+ * returns the end point on an iso-eta surface and the redshift decomposition
+ * of Eqs. (23)-(28) with no velocity terms.
+ *
+ * Units: c = 1, lengths and conformal time in h^-1 Mpc, phi = Phi / c^2.
+ *
+ * Ownership: every buffer passed in stays owned by the caller; the library
+ * owns what mt_build_octree allocates until mt_free.  All GPU work is
+ * enqueued on the CUDA stream given as `stream` (a cudaStream_t, NULL for the
+ * legacy default stream); functions return once the work is enqueued unless
+ * stated otherwise.  Calls that use the same octree must be ordered on one
+ * stream (they share the octree's small device work area).
+ *
+ * Errors: functions return an mt_status.  Host-side validation failures
+ * return MT_ERR_INVALID_ARG (or the specific code below) before any GPU work
+ * is enqueued.  Per-ray outcomes are in the `status` output; kernel-level
+ * faults (a hash probe run that exceeds the table) set a device flag read by
+ * mt_device_status.
+ */
+#ifndef MT_H
+#define MT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MT_OK = 0,
+  MT_ERR_INVALID_ARG = 1,   /* a pointer, size, layout or parameter is invalid */
+  MT_ERR_OOM = 2,           /* device memory allocation failed */
+  MT_ERR_CUDA = 3,          /* a CUDA runtime call failed (no device, launch failure, ...) */
+  MT_ERR_NOT_FULL_TREE = 4, /* keys unsorted, an octet incomplete or a parent missing (Sect. 2.1) */
+  MT_ERR_TIMEOUT = 5,       /* a device-side iteration bound was reached */
+  MT_ERR_OOB = 6,           /* a device-side index check failed */
+  MT_ERR_UNSUPPORTED = 7    /* valid request this build does not handle (limits below) */
+} mt_status;
+
+/* field precision of the octree records */
+enum { MT_FIELD_FP64 = 0, MT_FIELD_FP32 = 1 };
+
+/* per-ray status values */
+enum { MT_RAY_OK = 0, MT_RAY_LEFT_DOMAIN = 1, MT_RAY_MAX_STEPS = 2, MT_RAY_NONFINITE = 3 };
+
+/* level-data residency */
+enum { MT_HOST = 0, MT_DEVICE_COPY = 1, MT_DEVICE_BORROW = 2 };
+
+/* limits of this build */
+#define MT_MAX_LEVELS 8    /* refined levels above the coarse grid */
+#define MT_MAX_SLICES 16   /* time slices */
+#define MT_MAX_CONES 256   /* light cones (observers) per trace call */
+
+typedef struct mt_octree mt_octree; /* opaque, library-owned */
+
+/*
+ * Grid description (Sect. 2.1).  Level l has N_l = n_coarse * 2^l cells per
+ * axis of size dx_l = box / N_l; n_coarse must be a power of two and
+ * N_{n_levels} <= 2^21.  Cell (i, j, k) of level l has the Morton key with
+ * bit 3b = bit b of i, bit 3b+1 = bit b of j, bit 3b+2 = bit b of k, so the
+ * 8 children of a cell with key K have keys 8K .. 8K+7.
+ */
+typedef struct {
+  double box;               /* comoving side of the (periodic) box, > 0 */
+  int32_t n_coarse;         /* N_0, power of two in [1, 2^20] */
+  int32_t n_levels;         /* refined levels, 0 .. MT_MAX_LEVELS */
+  int32_t periodic;         /* 1: positions wrap into the box; 0: rays stop at the box edge */
+  int32_t n_slices;         /* time slices, 1 .. MT_MAX_SLICES */
+  const double* slice_eta;  /* host [n_slices], strictly ascending conformal times */
+  int32_t precision;        /* MT_FIELD_FP64 (double records) or MT_FIELD_FP32 (float records) */
+  int32_t pad;
+} mt_grid_desc;
+
+/*
+ * Cells of one level.  Level 0 must hold all N_0^3 cells in Morton order
+ * (keys 0 .. N_0^3 - 1; `keys` may be NULL there).  A refined level holds
+ * whole octets: count is a multiple of 8, keys strictly ascending, each
+ * octet's keys are 8K .. 8K+7, and its parent K exists on the level below
+ * (the full-tree rule of Sect. 2.1).
+ * records: [count][n_slices][4] of double (FP64) or float (FP32):
+ *          phi, d phi/dx, d phi/dy, d phi/dz per cell and slice.
+ */
+typedef struct {
+  const uint64_t* keys;   /* [count] */
+  const void* records;    /* [count][n_slices][4] */
+  int64_t count;
+  int32_t residency;      /* MT_HOST, MT_DEVICE_COPY, or MT_DEVICE_BORROW (device data kept by
+                             reference; it must outlive the octree and must not change) */
+  int32_t pad;
+} mt_level_data;
+
+/*
+ * mt_build_octree -- validate a full octree and build the device structure:
+ * per-level record arrays in Morton order, the coarse level directly indexed,
+ * each refined level behind an open-addressing hash from the parent key to its
+ * octet (Sect. 2.1: flattened AMR with a unique binary index per cell).
+ *
+ * bg_table: host [bg_n][4] nodes (eta_j, a_j, H_j, dH/deta_j) of the
+ * background (H = a'/a), strictly ascending and uniformly spaced in eta
+ * (Sect. 2.2: a(eta) and a'(eta) from external pre-computed tables); the last
+ * node is the observer's time eta_o (a = 1).  The library interpolates
+ * a(eta) and H(eta) by cubic Hermite with slopes a H and dH/deta.
+ *
+ * levels: [n_levels + 1].  On success *out receives the handle.  Synchronous:
+ * returns after the device structure is built and validated.
+ * Errors: MT_ERR_INVALID_ARG (descriptor), MT_ERR_NOT_FULL_TREE, MT_ERR_OOM,
+ * MT_ERR_CUDA.  On error *out is NULL and nothing stays allocated.
+ */
+mt_status mt_build_octree(const mt_grid_desc* grid, const mt_level_data* levels, const double* bg_table,
+                          int32_t bg_n, void* stream, mt_octree** out);
+
+/*
+ * Trace parameters.  Rays [ray_begin[c], ray_begin[c+1]) belong to cone c
+ * with observer observer[c] at eta_o and stop on the iso-eta surface
+ * eta_stop(c) = eta(a = 1 / (1 + z_max[c])) (Sect. 2.4 stop criterion, here
+ * p = eta), found by bisection on the background interpolant.
+ */
+typedef struct {
+  int32_t n_cones;          /* 1 .. MT_MAX_CONES */
+  int32_t steps_per_cell;   /* N >= 1 (Sect. 2.2; 4 in common settings) */
+  int32_t gravity_on;       /* 0: phi = 0 (FLRW / Born trajectories, Sect. 2.2), 1: full equations */
+  int32_t pad;
+  const double* observer;   /* host [n_cones][3] */
+  const double* z_max;      /* host [n_cones], >= 0 */
+  const int64_t* ray_begin; /* host [n_cones + 1], ray_begin[0] = 0, non-decreasing */
+  int64_t max_steps;        /* per-ray step cap (> 0); reaching it sets MT_RAY_MAX_STEPS */
+} mt_trace_params;
+
+/*
+ * Per-ray outputs, caller-owned DEVICE buffers of length N (x: [3][N],
+ * k: [4][N]).  Any pointer may be NULL to skip that output.
+ *   x       end position, unwrapped comoving coordinates
+ *   k       end wave vector k^0, k^1, k^2, k^3 (k^0 < 0: past-directed)
+ *   eta     end conformal time; lambda: affine parameter reached
+ *   chi     |x - x_o|; path: integral of |k| d lambda
+ *   z0, z1, z4, z5   Eqs. (23), (24), (27), (28) with v = 0 (a_o = 1)
+ *   d_a     a_s chi; d_l = (1 + z5)^2 d_a
+ *   phi_o, phi_s     interpolated potential at the observer / end point
+ *   isw     integral of d phi / d eta over eta from eta_s to eta_o (Eq. 27)
+ *   n_steps RK4 steps taken; level: most refined level containing the end point
+ *   status  MT_RAY_*
+ */
+typedef struct {
+  double* x;
+  double* k;
+  double* eta;
+  double* lambda;
+  double* chi;
+  double* path;
+  double* z0;
+  double* z1;
+  double* z4;
+  double* z5;
+  double* d_a;
+  double* d_l;
+  double* phi_o;
+  double* phi_s;
+  double* isw;
+  int32_t* n_steps;
+  int32_t* level;
+  int32_t* status;
+} mt_ray_out;
+
+/*
+ * mt_trace_rays -- integrate n_rays null geodesics (Sect. 2.2).
+ * dirs: device [3][n_rays] unit observed directions n (the ray starts with
+ * k^0 = -1, k^i = n sqrt((1 + 2 phi_o)/(1 - 2 phi_o)), the null condition).
+ * One persistent launch serves every cone; warps pull rays from a device
+ * queue as rays finish.  FP64 octrees integrate and interpolate in double;
+ * FP32 octrees interpolate in float and keep the ray state in double.
+ * Errors: MT_ERR_INVALID_ARG (parameters, NULL tree/dirs), MT_ERR_CUDA.
+ */
+mt_status mt_trace_rays(const mt_octree* tree, const mt_trace_params* params, const double* dirs, int64_t n_rays,
+                        const mt_ray_out* out, void* stream);
+
+/*
+ * mt_device_status -- synchronise `stream` and return the device-side flag of
+ * the last kernels on this octree (MT_OK, MT_ERR_OOB, MT_ERR_TIMEOUT), then
+ * clear it.
+ */
+mt_status mt_device_status(const mt_octree* tree, void* stream);
+
+/* mt_free -- release everything mt_build_octree allocated (NULL is ignored).
+ * The caller must make sure no enqueued work still uses the octree. */
+void mt_free(mt_octree* tree);
+
+/* mt_status_str -- static description of a status code. */
+const char* mt_status_str(mt_status s);
+
+/* mt_octree_info -- level counts and device bytes held (for reporting). */
+mt_status mt_octree_info(const mt_octree* tree, int64_t* cells_per_level /* [n_levels+1] or NULL */,
+                         int64_t* device_bytes /* or NULL */);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MT_H */

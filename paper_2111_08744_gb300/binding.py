@@ -1,0 +1,268 @@
+"""ctypes binding of libmt.so (include/mt.h): same names, argument marshalling only.
+
+Every step of the ray tracing runs in the CUDA library; torch supplies device
+buffers and the stream handle.  There is no CPU fallback: if libmt.so is missing
+or no CUDA device is visible, `load()` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Dict, Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmt.so")
+
+MT_OK, MT_ERR_INVALID_ARG, MT_ERR_OOM, MT_ERR_CUDA, MT_ERR_NOT_FULL_TREE, MT_ERR_TIMEOUT, MT_ERR_OOB, \
+    MT_ERR_UNSUPPORTED = range(8)
+MT_FIELD_FP64, MT_FIELD_FP32 = 0, 1
+MT_RAY_OK, MT_RAY_LEFT_DOMAIN, MT_RAY_MAX_STEPS, MT_RAY_NONFINITE = 0, 1, 2, 3
+MT_HOST, MT_DEVICE_COPY, MT_DEVICE_BORROW = 0, 1, 2
+MT_MAX_LEVELS, MT_MAX_SLICES, MT_MAX_CONES = 8, 16, 256
+
+
+class MtError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_str(code)} (code {code})")
+
+
+class mt_grid_desc(ctypes.Structure):
+    _fields_ = [("box", ctypes.c_double), ("n_coarse", ctypes.c_int32), ("n_levels", ctypes.c_int32),
+                ("periodic", ctypes.c_int32), ("n_slices", ctypes.c_int32), ("slice_eta", ctypes.c_void_p),
+                ("precision", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class mt_level_data(ctypes.Structure):
+    _fields_ = [("keys", ctypes.c_void_p), ("records", ctypes.c_void_p), ("count", ctypes.c_int64),
+                ("residency", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class mt_trace_params(ctypes.Structure):
+    _fields_ = [("n_cones", ctypes.c_int32), ("steps_per_cell", ctypes.c_int32), ("gravity_on", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("observer", ctypes.c_void_p), ("z_max", ctypes.c_void_p),
+                ("ray_begin", ctypes.c_void_p), ("max_steps", ctypes.c_int64)]
+
+
+OUT_F64 = ["x", "k", "eta", "lambda", "chi", "path", "z0", "z1", "z4", "z5", "d_a", "d_l", "phi_o", "phi_s", "isw"]
+OUT_I32 = ["n_steps", "level", "status"]
+OUT_ROWS = {"x": 3, "k": 4}
+
+
+class mt_ray_out(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in OUT_F64 + OUT_I32]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Load libmt.so (built by `paper_2111_08744_gb300.build.build()`); raise if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
+        lib = ctypes.CDLL(LIB_PATH)
+        P = ctypes.c_void_p
+        lib.mt_build_octree.restype = ctypes.c_int
+        lib.mt_build_octree.argtypes = [ctypes.POINTER(mt_grid_desc), ctypes.POINTER(mt_level_data), P,
+                                        ctypes.c_int32, P, ctypes.POINTER(P)]
+        lib.mt_trace_rays.restype = ctypes.c_int
+        lib.mt_trace_rays.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64,
+                                      ctypes.POINTER(mt_ray_out), P]
+        lib.mt_device_status.restype = ctypes.c_int
+        lib.mt_device_status.argtypes = [P, P]
+        lib.mt_free.restype = None
+        lib.mt_free.argtypes = [P]
+        lib.mt_status_str.restype = ctypes.c_char_p
+        lib.mt_status_str.argtypes = [ctypes.c_int]
+        lib.mt_octree_info.restype = ctypes.c_int
+        lib.mt_octree_info.argtypes = [P, P, P]
+        _lib = lib
+        return lib
+
+
+def status_str(code: int) -> str:
+    try:
+        return load().mt_status_str(int(code)).decode()
+    except Exception:
+        return f"status {code}"
+
+
+def _check(code: int, where: str):
+    if code != MT_OK:
+        raise MtError(code, where)
+
+
+def _require_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the ray tracer runs only on the GPU (no CPU fallback)")
+    return torch
+
+
+def _stream_handle(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+# ----------------------------------------------------------------------------- raw C-ABI names
+
+def mt_build_octree(grid, levels, bg_table, bg_n, stream, out):
+    return load().mt_build_octree(grid, levels, bg_table, bg_n, stream, out)
+
+
+def mt_trace_rays(tree, params, dirs, n_rays, out, stream):
+    return load().mt_trace_rays(tree, params, dirs, n_rays, out, stream)
+
+
+def mt_device_status(tree, stream):
+    return load().mt_device_status(tree, stream)
+
+
+def mt_free(tree):
+    load().mt_free(tree)
+
+
+def mt_status_str(code):
+    return status_str(code)
+
+
+# ----------------------------------------------------------------------------- helpers
+
+class Octree:
+    """Owns an mt_octree handle built from a workload's levels (host numpy or CUDA tensors)."""
+
+    def __init__(self, box, n_coarse, periodic, slice_eta, levels, bg, precision="fp32", stream=None,
+                 residency=None):
+        torch = _require_cuda()
+        lib = load()
+        self.precision = MT_FIELD_FP32 if precision in ("fp32", MT_FIELD_FP32) else MT_FIELD_FP64
+        rdt = np.float32 if self.precision == MT_FIELD_FP32 else np.float64
+        tdt = torch.float32 if self.precision == MT_FIELD_FP32 else torch.float64
+        self._keep = []
+        seta = np.ascontiguousarray(slice_eta, dtype=np.float64)
+        self._keep.append(seta)
+        n_levels = len(levels) - 1
+        g = mt_grid_desc(float(box), int(n_coarse), n_levels, int(periodic), int(seta.size),
+                         seta.ctypes.data_as(ctypes.c_void_p), self.precision, 0)
+        arr = (mt_level_data * len(levels))()
+        for i, lv in enumerate(levels):
+            keys, rec = lv.keys, lv.records
+            if isinstance(rec, torch.Tensor):
+                rec = rec.to(tdt).contiguous()
+                k = keys.contiguous() if isinstance(keys, torch.Tensor) else \
+                    torch.from_numpy(np.ascontiguousarray(keys, dtype=np.uint64).view(np.int64)).cuda()
+                self._keep += [rec, k]
+                arr[i] = mt_level_data(k.data_ptr(), rec.data_ptr(), int(k.numel()),
+                                       MT_DEVICE_COPY if residency is None else residency, 0)
+            else:
+                k = np.ascontiguousarray(keys, dtype=np.uint64)
+                r = np.ascontiguousarray(rec, dtype=rdt)
+                self._keep += [k, r]
+                arr[i] = mt_level_data(k.ctypes.data_as(ctypes.c_void_p), r.ctypes.data_as(ctypes.c_void_p),
+                                       int(k.size), MT_HOST, 0)
+        b = np.ascontiguousarray(bg, dtype=np.float64)
+        self._keep.append(b)
+        h = ctypes.c_void_p()
+        code = lib.mt_build_octree(ctypes.byref(g), arr, b.ctypes.data_as(ctypes.c_void_p), int(b.shape[0]),
+                                   _stream_handle(stream), ctypes.byref(h))
+        # host buffers may be released once the (synchronous) build returned
+        self._keep = [x for x in self._keep if isinstance(x, torch.Tensor)] if residency == MT_DEVICE_BORROW else []
+        _check(code, "mt_build_octree")
+        self.handle = h
+        self.n_levels = n_levels
+        self.n_slices = int(seta.size)
+
+    @classmethod
+    def from_workload(cls, w, precision="fp32", stream=None):
+        return cls(w.box, w.n_coarse, w.periodic, w.slice_eta, w.levels, w.bg, precision, stream)
+
+    def info(self):
+        cells = (ctypes.c_int64 * (self.n_levels + 1))()
+        nbytes = ctypes.c_int64()
+        _check(load().mt_octree_info(self.handle, cells, ctypes.byref(nbytes)), "mt_octree_info")
+        return list(cells), int(nbytes.value)
+
+    def device_status(self, stream=None) -> int:
+        return load().mt_device_status(self.handle, _stream_handle(stream))
+
+    def free(self):
+        if getattr(self, "handle", None):
+            load().mt_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class TraceParams:
+    """Host-side cone table for mt_trace_params."""
+
+    def __init__(self, observer, z_max, ray_begin, steps_per_cell=4, gravity_on=True, max_steps=1 << 22):
+        self.obs = np.ascontiguousarray(np.asarray(observer, dtype=np.float64).reshape(-1, 3))
+        self.zmax = np.ascontiguousarray(np.atleast_1d(np.asarray(z_max, dtype=np.float64)))
+        self.begin = np.ascontiguousarray(np.asarray(ray_begin, dtype=np.int64))
+        self.c = mt_trace_params(int(self.obs.shape[0]), int(steps_per_cell), 1 if gravity_on else 0, 0,
+                                 self.obs.ctypes.data_as(ctypes.c_void_p), self.zmax.ctypes.data_as(ctypes.c_void_p),
+                                 self.begin.ctypes.data_as(ctypes.c_void_p), int(max_steps))
+
+    @classmethod
+    def from_workload(cls, w, gravity_on=True, max_steps=None, steps_per_cell=None, ray_begin=None):
+        spc = w.steps_per_cell if steps_per_cell is None else steps_per_cell
+        if max_steps is None:
+            max_steps = step_cap(w.bg, w.box / w.n_coarse, len(w.levels) - 1, spc, float(np.max(w.z_max)))
+        return cls(w.observer, w.z_max, w.ray_begin if ray_begin is None else ray_begin, spc, gravity_on, max_steps)
+
+
+def step_cap(bg, dx0, n_levels, steps_per_cell, z_max):
+    """A per-ray step cap from the geometry: twice the steps a ray needs if it stayed on the
+    finest level all the way to z_max, plus a margin (a bound, not an estimate)."""
+    a_t = 1.0 / (1.0 + z_max)
+    eta = np.asarray(bg)[:, 0]
+    a = np.asarray(bg)[:, 1]
+    span = eta[-1] - float(np.interp(a_t, a, eta))
+    return int(2.0 * span * steps_per_cell * (1 << n_levels) / dx0) + 1024
+
+
+def alloc_outputs(n: int, device=None, names=None) -> Dict[str, "object"]:
+    torch = _require_cuda()
+    names = OUT_F64 + OUT_I32 if names is None else names
+    out = {}
+    for k in names:
+        dt = torch.int32 if k in OUT_I32 else torch.float64
+        shape = (OUT_ROWS[k], n) if k in OUT_ROWS else (n,)
+        out[k] = torch.empty(shape, dtype=dt, device=device or "cuda")
+    return out
+
+
+def ray_out_struct(out: Dict[str, "object"]) -> mt_ray_out:
+    return mt_ray_out(**{k: (out[k].data_ptr() if k in out and out[k] is not None else None)
+                         for k in OUT_F64 + OUT_I32})
+
+
+def trace_rays(tree: Octree, params: TraceParams, dirs, out=None, stream=None):
+    """mt_trace_rays on CUDA tensors: dirs float64 [3, N]; returns the output dict (device tensors)."""
+    torch = _require_cuda()
+    if not (isinstance(dirs, torch.Tensor) and dirs.is_cuda and dirs.dtype == torch.float64 and dirs.dim() == 2
+            and dirs.shape[0] == 3 and dirs.is_contiguous()):
+        raise ValueError("dirs must be a contiguous float64 CUDA tensor of shape [3, N]")
+    n = int(dirs.shape[1])
+    if out is None:
+        out = alloc_outputs(n, dirs.device)
+    o = ray_out_struct(out)
+    code = load().mt_trace_rays(tree.handle, ctypes.byref(params.c), dirs.data_ptr(), n, ctypes.byref(o),
+                                _stream_handle(stream))
+    _check(code, "mt_trace_rays")
+    return out

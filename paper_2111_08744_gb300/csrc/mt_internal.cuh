@@ -1,0 +1,321 @@
+// Device-side data layout and helpers of the GB300 ray tracer (sm_103a).
+//
+// Octree (Sect. 2.1, flattened AMR with a binary cell index):
+//   * level 0: dense N_0^3 record array in Morton order, indexed directly by key;
+//   * level l >= 1: whole octets, records in key order (octet o holds rows 8o..8o+7,
+//     child c = key & 7), plus an open-addressing hash  parent key -> octet index.
+//     A CIC neighbourhood at level l spans 1, 2, 4 or 8 octets, so one hash probe
+//     serves up to 8 corner cells.
+// Records: [count][S] of dvec4 (FP64 field) or float4 (FP32 field) holding
+//   phi, dphi/dx, dphi/dy, dphi/dz per slice; the two bracketing slices of a cell
+//   are adjacent in memory.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mt.h"
+
+namespace mt {
+
+constexpr int kMaxLevels = MT_MAX_LEVELS;
+constexpr int kMaxSlices = MT_MAX_SLICES;
+constexpr int kMaxCones = MT_MAX_CONES;
+constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr unsigned long long kHashMul = 0x9E3779B97F4A7C15ull;  // Fibonacci hashing (Knuth)
+
+enum : unsigned { kErrOOB = 1u, kErrTimeout = 2u, kErrTree = 4u };
+
+// 4 doubles, 16-byte aligned (records and background nodes)
+struct alignas(16) dvec4 {
+  double x, y, z, w;
+};
+
+struct HashTable {
+  const ulonglong2* slots;  // {key, octet index}; empty slots hold kEmptyKey
+  unsigned long long mask;  // capacity - 1 (capacity a power of two)
+  int shift;                // 64 - log2(capacity)
+  int pad;
+};
+
+struct DevField {
+  const void* rec[kMaxLevels + 1];
+  HashTable hash[kMaxLevels + 1];  // [0] unused
+  double box;
+  double dx0;       // box / N_0
+  double inv_dx0;   // N_0 / box (mixed path only)
+  int nc;           // N_0
+  int L;            // refined levels
+  int periodic;
+  int S;            // slices
+  double seta[kMaxSlices];
+  const dvec4* bg;  // (eta, a, H, dH/deta) nodes, uniform in eta
+  int bg_n;
+  int pad;
+  double bg_eta0, bg_deta, bg_inv_deta;
+  double eta_o;     // observer time = last background node
+};
+
+struct DevCones {
+  int n;
+  int pad;
+  long long begin[kMaxCones + 1];
+  double obs[kMaxCones][3];
+  double eta_stop[kMaxCones];
+};
+
+// ----------------------------------------------------------------- Morton keys
+
+__host__ __device__ __forceinline__ unsigned long long spread_bits3(unsigned long long v) {
+  v &= 0x1fffffull;
+  v = (v | (v << 32)) & 0x1f00000000ffffull;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+  v = (v | (v << 8)) & 0x100f00f00f00f00full;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+
+__host__ __device__ __forceinline__ unsigned long long morton(unsigned i, unsigned j, unsigned k) {
+  return spread_bits3(i) | (spread_bits3(j) << 1) | (spread_bits3(k) << 2);
+}
+
+// ----------------------------------------------------------------- hash
+
+__device__ __forceinline__ long long hash_find(const HashTable& t, unsigned long long key, unsigned* err) {
+  unsigned long long h = (key * kHashMul) >> t.shift;
+  for (unsigned long long probe = 0; probe <= t.mask; ++probe) {
+    ulonglong2 s = __ldg(&t.slots[h]);
+    if (s.x == key) return (long long)s.y;
+    if (s.x == kEmptyKey) return -1;
+    h = (h + 1) & t.mask;
+  }
+  atomicOr(err, kErrOOB);  // a table with no empty slot: cannot happen at load <= 1/2
+  return -1;
+}
+
+// ----------------------------------------------------------------- read-only vector loads
+
+__device__ __forceinline__ dvec4 ldg4(const dvec4* p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  const double2 a = __ldg(q), b = __ldg(q + 1);
+  return dvec4{a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
+
+// ----------------------------------------------------------------- background (Sect. 2.2 tables)
+
+// Cubic Hermite interpolation of a(eta) (slopes a H) and H(eta) (slopes dH/deta).
+__device__ __forceinline__ void bg_eval(const DevField& F, double eta, double* a, double* H) {
+  double t0 = (eta - F.bg_eta0) * F.bg_inv_deta;
+  double jf = floor(t0);
+  jf = fmin(fmax(jf, 0.0), (double)(F.bg_n - 2));
+  int j = (int)jf;
+  double t = t0 - jf;
+  dvec4 p = ldg4(&F.bg[j]);
+  dvec4 q = ldg4(&F.bg[j + 1]);
+  double d = F.bg_deta;
+  double t2 = t * t, t3 = t2 * t;
+  double h00 = 2.0 * t3 - 3.0 * t2 + 1.0;
+  double h10 = t3 - 2.0 * t2 + t;
+  double h01 = -2.0 * t3 + 3.0 * t2;
+  double h11 = t3 - t2;
+  if (a) *a = h00 * p.y + h10 * d * (p.y * p.z) + h01 * q.y + h11 * d * (q.y * q.z);
+  if (H) *H = h00 * p.z + h10 * d * p.w + h01 * q.z + h11 * d * q.w;
+}
+
+// ----------------------------------------------------------------- field sampling
+
+template <class T>
+struct Vec4;
+template <>
+struct Vec4<double> {
+  using type = dvec4;
+};
+template <>
+struct Vec4<float> {
+  using type = float4;
+};
+
+// Coarse-cell coordinates u = x / dx_0 (IEEE division in the FP64 path, a reciprocal
+// multiply in the mixed path), wrapped into [0, N_0) when periodic.  Returns false when
+// the point is outside a non-periodic box.
+template <class T>
+__device__ __forceinline__ bool coarse_coords(const DevField& F, const double* x, double* u) {
+  const double nc = (double)F.nc;
+  bool inside = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double v = (sizeof(T) == 8) ? x[d] / F.dx0 : x[d] * F.inv_dx0;
+    if (F.periodic) {
+      v = v - nc * floor(v * (1.0 / nc));
+    } else {
+      inside = inside && (v >= 0.0) && (v < nc);
+    }
+    u[d] = v;
+  }
+  return inside;
+}
+
+// Most refined level whose cell contains the point (Sect. 2.2 step 1): level l + 1
+// exists there iff the level-l cell containing it has children (one hash probe).
+__device__ __forceinline__ int locate_level(const DevField& F, const double* u, unsigned* err) {
+  int lf = 0;
+  const unsigned nc = (unsigned)F.nc;
+  for (int l = 1; l <= F.L; ++l) {
+    const double s = (double)(1u << (l - 1));
+    const unsigned m = (nc << (l - 1)) - 1u;
+    unsigned c0 = (unsigned)(long long)floor(u[0] * s) & m;
+    unsigned c1 = (unsigned)(long long)floor(u[1] * s) & m;
+    unsigned c2 = (unsigned)(long long)floor(u[2] * s) & m;
+    if (hash_find(F.hash[l], morton(c0, c1, c2), err) < 0) break;
+    lf = l;
+  }
+  return lf;
+}
+
+// CIC (Eq. 8) at level l with the two bracketing slices s, s+1 (or slice 0 when S = 1):
+// out[0..3] at slice s, out[4..7] at slice s+1.  Returns false if a neighbour is absent.
+template <class T>
+__device__ __forceinline__ bool cic_level(const DevField& F, int l, const double* u, int s, T* out, unsigned* err) {
+  using V = typename Vec4<T>::type;
+  const long long Nl = (long long)F.nc << l;
+  const double sc = (double)(1ll << l);
+  long long i0[3];
+  T f[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double U = u[d] * sc - 0.5;
+    double fl = floor(U);
+    i0[d] = (long long)fl;
+    f[d] = (T)(U - fl);
+  }
+  // wrapped corner coordinates a[d][c] for c = 0, 1
+  unsigned a[3][2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      long long v = i0[d] + c;
+      if (F.periodic) {
+        v &= (Nl - 1);
+      } else if (v < 0 || v >= Nl) {
+        return false;
+      }
+      a[d][c] = (unsigned)v;
+    }
+  }
+  long long rows[8];
+  if (l == 0) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) rows[c] = (long long)morton(a[0][c & 1], a[1][(c >> 1) & 1], a[2][(c >> 2) & 1]);
+  } else {
+    // parents of the two corners per axis coincide iff the lower corner index is even
+    const int ox = (int)(i0[0] & 1), oy = (int)(i0[1] & 1), oz = (int)(i0[2] & 1);
+    long long oct[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int qx = q & 1, qy = (q >> 1) & 1, qz = (q >> 2) & 1;
+      if ((qx && !ox) || (qy && !oy) || (qz && !oz)) {
+        oct[q] = -1;
+        continue;
+      }
+      const unsigned long long pk = morton(a[0][qx] >> 1, a[1][qy] >> 1, a[2][qz] >> 1);
+      oct[q] = hash_find(F.hash[l], pk, err);
+      if (oct[q] < 0) return false;
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+      const int q = (ox ? cx : 0) | ((oy ? cy : 0) << 1) | ((oz ? cz : 0) << 2);
+      const unsigned child = (a[0][cx] & 1u) | ((a[1][cy] & 1u) << 1) | ((a[2][cz] & 1u) << 2);
+      rows[c] = oct[q] * 8 + (long long)child;
+    }
+  }
+  const V* rec = (const V*)F.rec[l];
+  const int S = F.S;
+  const int s1 = (S > 1) ? s + 1 : s;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) out[q] = (T)0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const T wx = (c & 1) ? f[0] : (T)1 - f[0];
+    const T wy = (c & 2) ? f[1] : (T)1 - f[1];
+    const T wz = (c & 4) ? f[2] : (T)1 - f[2];
+    const T w = wx * wy * wz;
+    const V r0 = ldg4(&rec[rows[c] * S + s]);
+    const V r1 = ldg4(&rec[rows[c] * S + s1]);
+    out[0] += w * r0.x;
+    out[1] += w * r0.y;
+    out[2] += w * r0.z;
+    out[3] += w * r0.w;
+    out[4] += w * r1.x;
+    out[5] += w * r1.y;
+    out[6] += w * r1.z;
+    out[7] += w * r1.w;
+  }
+  return true;
+}
+
+// Field at (x, eta): phi, grad phi and d phi/d eta, with the level fallback of Sect. 2.2
+// (start at the most refined level containing the photon; while one of the 8 CIC
+// neighbours is missing, retry one level coarser).  Time: linear in eta between the
+// bracketing slices, extended linearly outside them.  *lf receives the most refined
+// level.  Returns false when the point is outside a non-periodic domain.
+template <class T>
+__device__ __forceinline__ bool sample_field(const DevField& F, const double* x, double eta, T* phi, T* g, T* pe,
+                                             int* lf, unsigned* err) {
+  double u[3];
+  if (!coarse_coords<T>(F, x, u)) return false;
+  const int lfin = locate_level(F, u, err);
+  *lf = lfin;
+  int s = 0;
+  while (s < F.S - 2 && F.seta[s + 1] <= eta) ++s;
+  T v[8];
+  int l = lfin;
+  for (; l >= 0; --l)
+    if (cic_level<T>(F, l, u, s, v, err)) break;
+  if (l < 0) return false;
+  if (F.S == 1) {
+    *phi = v[0];
+    g[0] = v[1];
+    g[1] = v[2];
+    g[2] = v[3];
+    *pe = (T)0;
+    return true;
+  }
+  const double de = F.seta[s + 1] - F.seta[s];
+  const T w = (T)((eta - F.seta[s]) / de);
+  const T ide = (T)(1.0 / de);
+  *phi = v[0] + w * (v[4] - v[0]);
+  g[0] = v[1] + w * (v[5] - v[1]);
+  g[1] = v[2] + w * (v[6] - v[2]);
+  g[2] = v[3] + w * (v[7] - v[3]);
+  *pe = (v[4] - v[0]) * ide;
+  return true;
+}
+
+}  // namespace mt
+
+// Library handle (host side).
+struct mt_octree {
+  int device;
+  int precision;
+  int n_levels;
+  int n_slices;
+  mt::DevField f;
+  void* rec_alloc[mt::kMaxLevels + 1];
+  ulonglong2* hash_alloc[mt::kMaxLevels + 1];
+  int64_t count[mt::kMaxLevels + 1];
+  double* bg_dev;
+  double* bg_host;
+  int bg_n;
+  unsigned long long* ws;  // [0] ray queue counter, [1] error flags
+  int64_t device_bytes;
+  int num_sms;
+};
+
+namespace mt {
+double host_eta_stop(const mt_octree* t, double z);
+void host_bg_eval(const double* tab, int n, double eta, double* a, double* H);
+}  // namespace mt

@@ -293,25 +293,31 @@ def spectral_laplacian(f: np.ndarray, box: float) -> np.ndarray:
 def trilinear_periodic(grid: np.ndarray, u: np.ndarray) -> np.ndarray:
     """Trilinear interpolation of a periodic cell-centred grid at points u [3, M] in cell units.
 
-    `grid` is [..., n, n, n]; leading axes are carried through.  Used only to
-    build refined-level inputs from coarser ones (the field model above).
+    `grid` is [n, n, n] or [n, n, n, C] (channels last); returns [M] or [M, C].  Used only
+    to build refined-level inputs from coarser ones (the field model above).  Runs on
+    multithreaded CPU torch ops for speed; FP64 throughout.
     """
-    n = grid.shape[-1]
-    v = u - 0.5
-    i0 = np.floor(v).astype(np.int64)
+    import torch
+
+    n = grid.shape[0]
+    flat = torch.from_numpy(np.ascontiguousarray(grid).reshape(n * n * n, -1))
+    v = torch.from_numpy(np.ascontiguousarray(u)) - 0.5
+    i0 = torch.floor(v)
     f = v - i0
-    out = 0.0
+    i0 = i0.to(torch.int64)
+    out = torch.zeros((u.shape[1], flat.shape[1]), dtype=torch.float64)
     for cx in (0, 1):
         wx = f[0] if cx else 1.0 - f[0]
-        ix = (i0[0] + cx) % n
+        ix = torch.remainder(i0[0] + cx, n) * (n * n)
         for cy in (0, 1):
-            wy = f[1] if cy else 1.0 - f[1]
-            iy = (i0[1] + cy) % n
+            wy = wx * (f[1] if cy else 1.0 - f[1])
+            iy = ix + torch.remainder(i0[1] + cy, n) * n
             for cz in (0, 1):
-                wz = f[2] if cz else 1.0 - f[2]
-                iz = (i0[2] + cz) % n
-                out = out + (wx * wy * wz) * grid[..., ix, iy, iz]
-    return out
+                w = wy * (f[2] if cz else 1.0 - f[2])
+                idx = iy + torch.remainder(i0[2] + cz, n)
+                out += w[:, None] * flat.index_select(0, idx)
+    out = out.numpy()
+    return out[:, 0] if grid.ndim == 3 else out
 
 
 # --------------------------------------------------------------------------
@@ -417,6 +423,8 @@ def build_field(n: int, box: float, n_levels: int, f1: float, ratio: float, seed
     ii, jj, kk = np.unravel_index(top, delta0.shape)
     parents = np.sort(morton3(ii, jj, kk))
     details = []
+    details4 = []
+    base4 = np.concatenate([phi0[..., None], np.moveaxis(grad0, 0, -1)], axis=-1)
     for lev in range(1, n_levels + 1):
         nl = n << lev
         dxl = box / nl
@@ -428,17 +436,14 @@ def build_field(n: int, box: float, n_levels: int, f1: float, ratio: float, seed
         d = gaussian_potential(tile, tbox, seed * 131 + lev, detail_rms, band=(0.5 * knyq, knyq * 1.0001))
         dgrad = gradient_5pt(d, dxl)
         details.append((d, dgrad))
+        details4.append(np.concatenate([d[..., None], np.moveaxis(dgrad, 0, -1)], axis=-1))
         # cell centres in coarse units and in each detail level's units
         xc = np.stack([ci + 0.5, cj + 0.5, ck + 0.5]).astype(np.float64) * dxl  # physical
-        rec = np.empty((keys.size, 4))
         u0 = xc / dx0
-        rec[:, 0] = trilinear_periodic(phi0, u0)
-        rec[:, 1:] = trilinear_periodic(grad0, u0).T
+        rec = trilinear_periodic(base4, u0)
         for m in range(1, lev):
-            dm, dgm = details[m - 1]
             um = xc / (box / (n << m))
-            rec[:, 0] += trilinear_periodic(dm, um)
-            rec[:, 1:] += trilinear_periodic(dgm, um).T
+            rec += trilinear_periodic(details4[m - 1], um)
         ti, tj, tk = ci % tile, cj % tile, ck % tile
         rec[:, 0] += d[ti, tj, tk]
         rec[:, 1:] += dgrad[:, ti, tj, tk].T

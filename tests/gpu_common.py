@@ -1,0 +1,52 @@
+"""Shared helpers of the GPU tests: run the CUDA path through the binding and compare with the oracle."""
+import numpy as np
+
+FLOAT_KEYS = ["x", "k", "eta", "lambda", "chi", "path", "z0", "z1", "z4", "z5", "d_a", "d_l", "phi_o", "phi_s", "isw"]
+INT_KEYS = ["n_steps", "level", "status"]
+# absolute floors of the relative error: lengths in h^-1 Mpc, redshifts, potentials, wave vector
+FLOORS = {"x": 1.0, "k": 1.0, "eta": 1.0, "lambda": 1.0, "chi": 1.0, "path": 1.0, "d_a": 1.0, "d_l": 1.0,
+          "z0": 1e-6, "z1": 1e-6, "z4": 1e-6, "z5": 1e-6, "phi_o": 1e-6, "phi_s": 1e-6, "isw": 1e-6}
+
+
+def run_gpu(w, precision="fp64", dirs=None, gravity_on=True, max_steps=None, levels=None, ray_begin=None):
+    import torch
+
+    from paper_2111_08744_gb300 import binding as B
+    from paper_2111_08744_gb300 import inputs as I
+
+    lv = w.levels if levels is None else levels
+    tree = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, lv, w.bg, precision)
+    d = w.dirs if dirs is None else dirs
+    p = B.TraceParams.from_workload(w, gravity_on=gravity_on, max_steps=max_steps,
+                                    ray_begin=ray_begin if ray_begin is not None else
+                                    (None if dirs is None else np.array([0, d.shape[1]])))
+    out = B.trace_rays(tree, p, torch.from_numpy(np.ascontiguousarray(d)).cuda())
+    torch.cuda.synchronize()
+    st = tree.device_status()
+    tree.free()
+    assert st == B.MT_OK, B.status_str(st)
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def rel_err(got, ref, key):
+    return np.abs(got - ref) / np.maximum(np.abs(ref), FLOORS[key])
+
+
+def compare(got, ref, rtol, exact_ints=True, idx=None, keys=None):
+    """Element-wise comparison; returns the max relative error per float output."""
+    errs = {}
+    for k in INT_KEYS:
+        g, r = got[k], ref[k]
+        if idx is not None:
+            g = g[..., idx]
+        if exact_ints:
+            bad = np.nonzero(g != r)[0]
+            assert bad.size == 0, f"{k} differs on {bad.size} rays, first {bad[:5]}: gpu {g[bad[:5]]} oracle {r[bad[:5]]}"
+    for k in (keys or FLOAT_KEYS):
+        g, r = got[k], ref[k]
+        if idx is not None:
+            g = g[..., idx]
+        e = rel_err(g, r, k)
+        errs[k] = float(e.max()) if e.size else 0.0
+        assert errs[k] <= rtol, f"{k}: max relative error {errs[k]:.3e} > {rtol:.1e}"
+    return errs
