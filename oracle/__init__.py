@@ -60,7 +60,7 @@ _OUT_I32 = ["n_steps", "level", "status"]
 
 
 class _Out(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_void_p) for n in _OUT_F64 + _OUT_I32]
+    _fields_ = [(n, ctypes.c_void_p) for n in _OUT_F64 + _OUT_I32 + ["tie"]]
 
 
 def _load():
@@ -122,7 +122,13 @@ def default_threads() -> int:
 
 
 def trace(w, dirs=None, levels=None, gravity_on=True, max_steps=10_000_000, n_threads=None, ray_begin=None):
-    """Trace rays of workload `w` (optionally other directions / a subset). Returns a dict of arrays."""
+    """Trace rays of workload `w` (optionally other directions / a subset). Returns a dict of arrays.
+
+    Besides the per-ray outputs of the method, "tie" is the smallest margin of any index
+    decision along the ray: the distance (in cell units) of a floor() argument to the
+    nearest integer in a locate or CIC step, or the relative margin of the stop test.  A ray
+    with a tie below ~1e-8 can take either side of a cell face under rounding alone.
+    """
     lib = _load()
     m = _Marshal(w, levels, gravity_on, max_steps)
     d = np.ascontiguousarray(w.dirs if dirs is None else dirs, dtype=np.float64)
@@ -137,6 +143,7 @@ def trace(w, dirs=None, levels=None, gravity_on=True, max_steps=10_000_000, n_th
         m.params.ray_begin = _ptr(m.begin)
     out = {k: np.zeros((3, n) if k == "x" else (4, n) if k == "k" else n) for k in _OUT_F64}
     out.update({k: np.zeros(n, dtype=np.int32) for k in _OUT_I32})
+    out["tie"] = np.ones(n)
     o = _Out(**{k: _ptr(v) for k, v in out.items()})
     rc = lib.orc_trace(ctypes.byref(m.grid), m.levels, _ptr(m.bg), int(m.bg.shape[0]), ctypes.byref(m.params),
                        _ptr(d), n, ctypes.byref(o), int(n_threads or default_threads()))

@@ -76,6 +76,8 @@ struct orc_out {
   int32_t* n_steps; // [N]
   int32_t* level;   // [N] most refined level containing the end point
   int32_t* status;  // [N] 0 ok, 1 left domain, 2 max steps, 3 non-finite
+  double* tie;      // [N] smallest margin of any index decision along the ray (cell units for
+                    //     locate/CIC floors, relative for the stop test); NULL to skip
 };
 
 }  // extern "C"
@@ -173,26 +175,33 @@ struct Field {
     if (p == e || *p != key) return -1;
     return (int64_t)(p - b);
   }
+  // distance of v to the nearest integer: how close a floor() decision came to a tie
+  static void note_tie(double v, double* tie) {
+    if (!tie) return;
+    double r = std::fabs(v - std::nearbyint(v));
+    if (r < *tie) *tie = r;
+  }
   // most refined level whose cell contains the point (-1: outside the domain)
-  int finest(const double* u) const {
+  int finest(const double* u, double* tie = nullptr) const {
     int best = -1;
     for (int l = 0; l <= L; ++l) {
       double s = std::ldexp(1.0, l);
       int64_t c[3];
-      for (int d = 0; d < 3; ++d) c[d] = (int64_t)std::floor(u[d] * s);
+      for (int d = 0; d < 3; ++d) { c[d] = (int64_t)std::floor(u[d] * s); note_tie(u[d] * s, tie); }
       if (find(l, c[0], c[1], c[2]) < 0) break;
       best = l;
     }
     return best;
   }
   // CIC (Eq. 8) of the 4 record components at slice s, level l; false when a neighbour is absent.
-  bool cic_level(int l, const double* u, double (*vals)[4]) const {
+  bool cic_level(int l, const double* u, double (*vals)[4], double* tie = nullptr) const {
     double s = std::ldexp(1.0, l);
     double U[3];
     int64_t i0[3];
     for (int d = 0; d < 3; ++d) {
       U[d] = u[d] * s;
       i0[d] = (int64_t)std::floor(U[d] - 0.5);
+      note_tie(U[d] - 0.5, tie);
     }
     int64_t rows[8];
     for (int c = 0; c < 8; ++c) {
@@ -218,13 +227,14 @@ struct Field {
   // Sect. 2.2 (start at the most refined level containing the photon, go coarser while a
   // neighbour is missing).  Time: linear in eta between the bracketing slices.
   // Returns false when even level 0 lacks neighbours (edge of a non-periodic domain).
-  bool sample(const double* u, double eta, double* phi, double* grad, double* phi_eta, int* lev_used) const {
-    int lf = finest(u);
+  bool sample(const double* u, double eta, double* phi, double* grad, double* phi_eta, int* lev_used,
+              double* tie = nullptr) const {
+    int lf = finest(u, tie);
     if (lf < 0) return false;
     double vals[64][4];
     int l = lf;
     for (; l >= 0; --l)
-      if (cic_level(l, u, vals)) break;
+      if (cic_level(l, u, vals, tie)) break;
     if (l < 0) return false;
     if (lev_used) *lev_used = l;
     if (S == 1) {
@@ -252,7 +262,7 @@ struct Tracer {
   int64_t max_steps;
 
   // Right-hand side of Eqs. (2)-(3) with d phi/d lambda from the chain rule, Eq. (4).
-  bool rhs(const double* y, double* dy) const {
+  bool rhs(const double* y, double* dy, double* tie) const {
     const double* x = y;
     double eta = y[3], k0 = y[4];
     const double* k = y + 5;
@@ -262,7 +272,7 @@ struct Tracer {
     if (gravity) {
       double u[3];
       f.coarse_coords(x, u);
-      if (!f.sample(u, eta, &phi, g, &pe, nullptr)) return false;
+      if (!f.sample(u, eta, &phi, g, &pe, nullptr, tie)) return false;
     }
     double dphidl = g[0] * k[0] + g[1] * k[1] + g[2] * k[2] + pe * k0;
     dy[0] = k[0];
@@ -281,6 +291,7 @@ struct Tracer {
     double y[10];
     double lambda, phi_o, phi_s;
     int n_steps, level, status;
+    double tie;
   };
 
   Result trace(const double* xo, const double* n, double eta_stop) const {
@@ -304,26 +315,33 @@ struct Tracer {
     r.phi_o = phi_o;
     r.n_steps = 0;
     r.status = ST_OK;
+    r.tie = 1.0;
     if (!(y[3] > eta_stop)) goto done;
     for (;;) {
       if (r.n_steps >= max_steps) { r.status = ST_MAXSTEPS; break; }
       double u[3];
       f.coarse_coords(y, u);
-      int lf = f.finest(u);
+      // decisions at the observer itself are exact on any implementation: not tracked
+      double* tie0 = r.n_steps > 0 ? &r.tie : nullptr;
+      int lf = f.finest(u, tie0);
       if (lf < 0) { r.status = ST_LEFT; break; }
       double k0 = y[4];
       double h = f.dx(lf) / ((double)N * std::fabs(k0));
       bool last = false;
+      {
+        double m = std::fabs((y[3] + k0 * h) - eta_stop) / std::fabs(k0 * h);
+        if (m < r.tie) r.tie = m;
+      }
       if (y[3] + k0 * h <= eta_stop) { h = (eta_stop - y[3]) / k0; last = true; }
       // classical RK4
       double k1[10], k2[10], k3[10], k4[10], t[10];
-      if (!rhs(y, k1)) { r.status = ST_LEFT; break; }
+      if (!rhs(y, k1, tie0)) { r.status = ST_LEFT; break; }
       for (int i = 0; i < 10; ++i) t[i] = y[i] + 0.5 * h * k1[i];
-      if (!rhs(t, k2)) { r.status = ST_LEFT; break; }
+      if (!rhs(t, k2, &r.tie)) { r.status = ST_LEFT; break; }
       for (int i = 0; i < 10; ++i) t[i] = y[i] + 0.5 * h * k2[i];
-      if (!rhs(t, k3)) { r.status = ST_LEFT; break; }
+      if (!rhs(t, k3, &r.tie)) { r.status = ST_LEFT; break; }
       for (int i = 0; i < 10; ++i) t[i] = y[i] + h * k3[i];
-      if (!rhs(t, k4)) { r.status = ST_LEFT; break; }
+      if (!rhs(t, k4, &r.tie)) { r.status = ST_LEFT; break; }
       for (int i = 0; i < 10; ++i) y[i] = y[i] + (h / 6.0) * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
       r.lambda += h;
       r.n_steps += 1;
@@ -338,7 +356,7 @@ struct Tracer {
     {
       double u[3];
       f.coarse_coords(y, u);
-      r.level = f.finest(u);
+      r.level = f.finest(u, &r.tie);
       if (gravity && r.status != ST_NONFINITE) {
         double g[3], pe;
         if (!f.sample(u, y[3], &r.phi_s, g, &pe, nullptr)) r.phi_s = 0.0;
@@ -469,6 +487,7 @@ int orc_trace(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n
     o->n_steps[i] = r.n_steps;
     o->level[i] = r.level;
     o->status[i] = r.status;
+    if (o->tie) o->tie[i] = r.tie;
   });
   return 0;
 }

@@ -126,7 +126,10 @@ __device__ void ray_init(const DevField& F, const DevCones& C, const double* __r
 // One RK4 step (Sect. 2.2).  Returns true when the ray is finished.
 template <class T>
 __device__ __forceinline__ bool ray_step(const DevField& F, const TraceArgs& A, RayState& r, unsigned* err) {
-  if (!(r.y[3] > r.eta_stop)) return true;
+  // a ray that starts on or past its stop surface takes no step; afterwards only the
+  // shortened last step ends the ray (a full step that overshoots eta_stop is followed by
+  // a short step back onto the surface)
+  if (r.n_steps == 0 && !(r.y[3] > r.eta_stop)) return true;
   if (r.n_steps >= A.max_steps) {
     r.status = MT_RAY_MAX_STEPS;
     return true;

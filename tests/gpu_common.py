@@ -3,6 +3,7 @@ import numpy as np
 
 FLOAT_KEYS = ["x", "k", "eta", "lambda", "chi", "path", "z0", "z1", "z4", "z5", "d_a", "d_l", "phi_o", "phi_s", "isw"]
 INT_KEYS = ["n_steps", "level", "status"]
+TIE_MARGIN = 1e-8
 # absolute floors of the relative error: lengths in h^-1 Mpc, redshifts, potentials, wave vector
 FLOORS = {"x": 1.0, "k": 1.0, "eta": 1.0, "lambda": 1.0, "chi": 1.0, "path": 1.0, "d_a": 1.0, "d_l": 1.0,
           "z0": 1e-6, "z1": 1e-6, "z4": 1e-6, "z5": 1e-6, "phi_o": 1e-6, "phi_s": 1e-6, "isw": 1e-6}
@@ -41,7 +42,16 @@ def compare(got, ref, rtol, exact_ints=True, idx=None, keys=None):
             g = g[..., idx]
         if exact_ints:
             bad = np.nonzero(g != r)[0]
-            assert bad.size == 0, f"{k} differs on {bad.size} rays, first {bad[:5]}: gpu {g[bad[:5]]} oracle {r[bad[:5]]}"
+            # a ray whose path grazes a cell face within rounding has two valid index sequences
+            # (two correct answers); every mismatch must be such a tie, and ties must be rare
+            tie = ref.get("tie")
+            if tie is not None and bad.size:
+                untied = bad[tie[bad] >= TIE_MARGIN]
+                assert untied.size == 0, (f"{k} differs on {untied.size} non-tie rays, first {untied[:5]}: "
+                                          f"gpu {g[untied[:5]]} oracle {r[untied[:5]]} tie {tie[untied[:5]]}")
+                assert bad.size <= max(2, 0.01 * g.size), f"{k}: too many tie mismatches ({bad.size})"
+            else:
+                assert bad.size == 0, f"{k} differs on {bad.size} rays, first {bad[:5]}: gpu {g[bad[:5]]} oracle {r[bad[:5]]}"
     for k in (keys or FLOAT_KEYS):
         g, r = got[k], ref[k]
         if idx is not None:

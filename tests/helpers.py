@@ -51,7 +51,9 @@ def workload(levels, box, n, dirs, z_max=0.5, observer=None, periodic=1, steps_p
         slice_eta = np.array([bg[-1, 0]])
     if slice_weight is None:
         slice_weight = np.ones(len(slice_eta))
-    obs = np.array([[0.5 * box] * 3]) if observer is None else np.asarray(observer, dtype=np.float64).reshape(-1, 3)
+    # default observer: near the centre but off every cell face (generic position)
+    obs = (np.array([[0.5 * box + 0.137 * box / n, 0.5 * box + 0.291 * box / n, 0.5 * box + 0.443 * box / n]])
+           if observer is None else np.asarray(observer, dtype=np.float64).reshape(-1, 3))
     dirs = np.ascontiguousarray(dirs, dtype=np.float64)
     return I.Workload(name=name, box=box, n_coarse=n, periodic=periodic, slice_eta=np.asarray(slice_eta, float),
                       slice_weight=np.asarray(slice_weight, float), levels=levels, bg=bg, omega_m=omega_m,
