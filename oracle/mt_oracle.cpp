@@ -356,7 +356,7 @@ struct Tracer {
     {
       double u[3];
       f.coarse_coords(y, u);
-      r.level = f.finest(u, &r.tie);
+      r.level = r.status == ST_NONFINITE ? -1 : f.finest(u, &r.tie);
       if (gravity && r.status != ST_NONFINITE) {
         double g[3], pe;
         if (!f.sample(u, y[3], &r.phi_s, g, &pe, nullptr)) r.phi_s = 0.0;

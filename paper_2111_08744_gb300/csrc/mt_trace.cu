@@ -201,7 +201,7 @@ __device__ void ray_finish(const DevField& F, const TraceArgs& A, const RayState
   double phi_s = 0.0;
   int lev = -1;
   double u[3];
-  if (coarse_coords<T>(F, y, u)) lev = locate_level(F, u, err);
+  if (r.status != MT_RAY_NONFINITE && coarse_coords<T>(F, y, u)) lev = locate_level(F, u, err);
   if (A.gravity_on && r.status != MT_RAY_NONFINITE) {
     T p, g[3], pe;
     int l;
