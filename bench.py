@@ -148,7 +148,7 @@ def run_reference(args, ws, rank):
         return
     import oracle
     from paper_2111_08744_gb300 import inputs as I
-    w = I.config_amr()
+    w = I.cached(I.config_amr)
     vals = []
     for i in range(args.warmup + args.steps):
         v, n, threads, dt = oracle_sample(w, budget_s=args.ref_budget)
@@ -174,7 +174,11 @@ def run_ours(args, ws, rank):
     from paper_2111_08744_gb300 import inputs as I
 
     Bd.build()
-    w = I.config_amr()
+    w = I.cached(I.config_amr)
+    if args.rays:
+        # a seeded subset of the rays (profiling captures of a short launch; not a bench line)
+        rng = np.random.Generator(np.random.PCG64(7))
+        w = I.with_rays(w, w.dirs[:, np.sort(rng.choice(w.n_rays, size=args.rays, replace=False))])
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
     levels32 = I.fp32_levels(w)
@@ -273,6 +277,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rays", type=int, default=0, help="trace a seeded subset of N rays (profiling only)")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":

@@ -528,6 +528,34 @@ def with_rays(w: Workload, dirs: np.ndarray, name: Optional[str] = None) -> Work
                                ray_begin=np.array([0, dirs.shape[1]], dtype=np.int64), name=name or w.name)
 
 
+def cached(builder, cache_dir: Optional[str] = None, **kwargs) -> Workload:
+    """builder(**kwargs), memoised on disk (pickle) under cache_dir or $MT_WORKLOAD_CACHE.
+
+    Generation of the large AMR fields takes tens of seconds; repeated processes on one
+    machine (tests, benchmark, profiler runs) reuse the pickled result.  No cache is used
+    when neither is set.
+    """
+    import hashlib
+    import os
+    import pickle
+
+    d = cache_dir or os.environ.get("MT_WORKLOAD_CACHE")
+    if not d:
+        return builder(**kwargs)
+    key = hashlib.sha1(repr((builder.__name__, sorted(kwargs.items()))).encode()).hexdigest()[:16]
+    path = os.path.join(d, f"{builder.__name__}_{key}.pkl")
+    if os.path.exists(path):
+        with open(path, "rb") as f:
+            return pickle.load(f)
+    w = builder(**kwargs)
+    os.makedirs(d, exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "wb") as f:
+        pickle.dump(w, f, protocol=pickle.HIGHEST_PROTOCOL)
+    os.replace(tmp, path)
+    return w
+
+
 def fp32_levels(w: Workload) -> List[Level]:
     """The same records rounded to float32 (the mixed-precision field)."""
     return [Level(keys=l.keys, records=l.records.astype(np.float32)) for l in w.levels]

@@ -33,7 +33,7 @@ def amr_small():
 @functools.lru_cache(maxsize=None)
 def amr_full():
     # the benchmark workload: 256^3 in 1 h^-1 Gpc + 3 levels (2%, 0.5%, 0.125%), 786,432 rays to z = 1
-    return I.config_amr()
+    return I.cached(I.config_amr)
 
 
 @functools.lru_cache(maxsize=None)
