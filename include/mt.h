@@ -184,6 +184,38 @@ mt_status mt_trace_rays(const mt_octree* tree, const mt_trace_params* params, co
                         const mt_ray_out* out, void* stream);
 
 /*
+ * mt_trace_rays_noalloc -- the same trace as mt_trace_rays, for callers that must not
+ * allocate GPU memory.  The paper has no counterpart: this is a property of this
+ * library's interface, not of the method.
+ *
+ * Who needs it: code that traces from inside a host application whose device memory is
+ * owned by another allocator (a framework's caching allocator that has reserved the
+ * GPU, or a serving process with a fixed device-memory budget), where a cudaMalloc would
+ * fail or is not allowed, and loops that cannot afford cudaMalloc/cudaFree, which may
+ * synchronise the whole device.  mt_trace_rays allocates nothing per call either, but its
+ * scratch lives in the octree; this entry point's scratch (the ray-queue counter and the
+ * cone table) is a static device array of this library, about 160 KiB, present on every
+ * GPU that loads the library until the process exits.  It calls no cudaMalloc, cudaFree
+ * or other allocating routine.
+ *
+ * Arguments, outputs and results are those of mt_trace_rays.  Because the cone table sits
+ * in the static array instead of the kernel's parameters, up to MT_NOALLOC_MAX_CONES cones
+ * are accepted; more return MT_ERR_UNSUPPORTED before any GPU work.
+ *
+ * The first call on a device looks up the static array's device address
+ * (cudaGetSymbolAddress, once per device, with the octree's device current); make that
+ * first call before any stream capture.  Every call clears the queue counter and rewrites
+ * the cone table on `stream`, copying the table from pageable host memory, so the call
+ * waits for earlier work on `stream` before it returns.  All calls share the one array:
+ * calls that overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Device-side faults are flagged in the octree's status word
+ * (mt_device_status).
+ */
+#define MT_NOALLOC_MAX_CONES 4096
+mt_status mt_trace_rays_noalloc(const mt_octree* tree, const mt_trace_params* params, const double* dirs,
+                                int64_t n_rays, const mt_ray_out* out, void* stream);
+
+/*
  * mt_device_status -- synchronise `stream` and return the device-side flag of
  * the last kernels on this octree (MT_OK, MT_ERR_OOB, MT_ERR_TIMEOUT), then
  * clear it.

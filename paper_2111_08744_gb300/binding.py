@@ -21,7 +21,7 @@ MT_OK, MT_ERR_INVALID_ARG, MT_ERR_OOM, MT_ERR_CUDA, MT_ERR_NOT_FULL_TREE, MT_ERR
 MT_FIELD_FP64, MT_FIELD_FP32 = 0, 1
 MT_RAY_OK, MT_RAY_LEFT_DOMAIN, MT_RAY_MAX_STEPS, MT_RAY_NONFINITE = 0, 1, 2, 3
 MT_HOST, MT_DEVICE_COPY, MT_DEVICE_BORROW = 0, 1, 2
-MT_MAX_LEVELS, MT_MAX_SLICES, MT_MAX_CONES = 8, 16, 256
+MT_MAX_LEVELS, MT_MAX_SLICES, MT_MAX_CONES, MT_NOALLOC_MAX_CONES = 8, 16, 256, 4096
 
 
 class MtError(RuntimeError):
@@ -76,6 +76,9 @@ def load():
         lib.mt_trace_rays.restype = ctypes.c_int
         lib.mt_trace_rays.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64,
                                       ctypes.POINTER(mt_ray_out), P]
+        lib.mt_trace_rays_noalloc.restype = ctypes.c_int
+        lib.mt_trace_rays_noalloc.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64,
+                                              ctypes.POINTER(mt_ray_out), P]
         lib.mt_device_status.restype = ctypes.c_int
         lib.mt_device_status.argtypes = [P, P]
         lib.mt_free.restype = None
@@ -122,6 +125,10 @@ def mt_build_octree(grid, levels, bg_table, bg_n, stream, out):
 
 def mt_trace_rays(tree, params, dirs, n_rays, out, stream):
     return load().mt_trace_rays(tree, params, dirs, n_rays, out, stream)
+
+
+def mt_trace_rays_noalloc(tree, params, dirs, n_rays, out, stream):
+    return load().mt_trace_rays_noalloc(tree, params, dirs, n_rays, out, stream)
 
 
 def mt_device_status(tree, stream):

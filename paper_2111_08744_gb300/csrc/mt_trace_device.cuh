@@ -1,0 +1,240 @@
+// Per-ray device code of the geodesic integrator (Sect. 2.2), shared by the trace kernels.
+//
+// State per ray: y = (x[3], eta, k0, k[3], I, s) in double, plus lambda.
+//   Field precision double: interpolation and right-hand side in double.
+//   Field precision float : in-cell fractions, weights, interpolation and the
+//     gravitational terms of the right-hand side in float; the background terms,
+//     the RK4 combination and the state stay double.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "mt_internal.cuh"
+
+namespace mt {
+
+struct OutPtrs {
+  double *x, *k, *eta, *lambda, *chi, *path, *z0, *z1, *z4, *z5, *d_a, *d_l, *phi_o, *phi_s, *isw;
+  int32_t *n_steps, *level, *status;
+};
+
+struct TraceArgs {
+  int steps_per_cell;
+  int gravity_on;
+  long long max_steps;
+  long long n_rays;
+};
+
+constexpr int kBlock = 128;
+
+// Geodesic right-hand side.  Returns false outside a non-periodic domain.  When lf is
+// non-null it receives the most refined level containing the point.
+template <class T>
+__device__ __forceinline__ bool geodesic_rhs(const DevField& F, bool grav, const double* y, double* dy, int* lf,
+                                             unsigned* err) {
+  double H;
+  bg_eval(F, y[3], nullptr, &H);
+  const double k0 = y[4];
+  const double k1 = y[5], k2 = y[6], k3 = y[7];
+  T phi = (T)0, g[3] = {(T)0, (T)0, (T)0}, pe = (T)0;
+  if (grav) {
+    int l;
+    if (!sample_field<T>(F, y, y[3], &phi, g, &pe, &l, err)) return false;
+    if (lf) *lf = l;
+  } else if (lf) {
+    double u[3];
+    if (!coarse_coords<T>(F, y, u)) return false;
+    *lf = locate_level(F, u, err);
+  }
+  dy[0] = k1;
+  dy[1] = k2;
+  dy[2] = k3;
+  dy[3] = k0;
+  const double bgk = -2.0 * H * k0;
+  if (sizeof(T) == 8) {
+    const double dphidl = (double)g[0] * k1 + (double)g[1] * k2 + (double)g[2] * k3 + (double)pe * k0;
+    dy[4] = bgk * k0 - 2.0 * dphidl * k0 + 2.0 * (double)pe * k0 * k0;
+    dy[5] = bgk * k1 + 2.0 * dphidl * k1 - 2.0 * (double)g[0] * k0 * k0;
+    dy[6] = bgk * k2 + 2.0 * dphidl * k2 - 2.0 * (double)g[1] * k0 * k0;
+    dy[7] = bgk * k3 + 2.0 * dphidl * k3 - 2.0 * (double)g[2] * k0 * k0;
+    dy[8] = -(double)pe * k0;
+    dy[9] = sqrt(k1 * k1 + k2 * k2 + k3 * k3);
+  } else {
+    const float fk0 = (float)k0, fk1 = (float)k1, fk2 = (float)k2, fk3 = (float)k3;
+    const float dphidl = (float)g[0] * fk1 + (float)g[1] * fk2 + (float)g[2] * fk3 + (float)pe * fk0;
+    const float k00 = fk0 * fk0;
+    dy[4] = bgk * k0 + (double)(-2.0f * dphidl * fk0 + 2.0f * (float)pe * k00);
+    dy[5] = bgk * k1 + (double)(2.0f * dphidl * fk1 - 2.0f * (float)g[0] * k00);
+    dy[6] = bgk * k2 + (double)(2.0f * dphidl * fk2 - 2.0f * (float)g[1] * k00);
+    dy[7] = bgk * k3 + (double)(2.0f * dphidl * fk3 - 2.0f * (float)g[2] * k00);
+    dy[8] = (double)(-(float)pe * fk0);
+    dy[9] = (double)sqrtf(fk1 * fk1 + fk2 * fk2 + fk3 * fk3);
+  }
+  return true;
+}
+
+struct RayState {
+  double y[10];
+  double lambda;
+  double phi_o;
+  double eta_stop;
+  double xo[3];
+  int n_steps;
+  int status;
+};
+
+// Initial state of a ray leaving observer xo at eta_o along dirs[:, ray] (Sect. 2.2):
+// k0 = -1 and k^i = n sqrt((1 + 2 phi_o)/(1 - 2 phi_o)) (null condition of Eq. 1).
+template <class T>
+__device__ void ray_start(const DevField& F, const double* xo, double eta_stop, const double* __restrict__ dirs,
+                          long long n, long long ray, bool grav, RayState& r, unsigned* err) {
+  r.xo[0] = xo[0];
+  r.xo[1] = xo[1];
+  r.xo[2] = xo[2];
+  r.eta_stop = eta_stop;
+  double phi_o = 0.0;
+  if (grav) {
+    T p, g[3], pe;
+    int l;
+    if (sample_field<T>(F, r.xo, F.eta_o, &p, g, &pe, &l, err)) phi_o = (double)p;
+  }
+  const double kn = sqrt((1.0 + 2.0 * phi_o) / (1.0 - 2.0 * phi_o));
+  r.y[0] = r.xo[0];
+  r.y[1] = r.xo[1];
+  r.y[2] = r.xo[2];
+  r.y[3] = F.eta_o;
+  r.y[4] = -1.0;
+  r.y[5] = __ldg(&dirs[ray]) * kn;
+  r.y[6] = __ldg(&dirs[n + ray]) * kn;
+  r.y[7] = __ldg(&dirs[2 * n + ray]) * kn;
+  r.y[8] = 0.0;
+  r.y[9] = 0.0;
+  r.lambda = 0.0;
+  r.phi_o = phi_o;
+  r.n_steps = 0;
+  r.status = MT_RAY_OK;
+}
+
+// One RK4 step (Sect. 2.2).  Returns true when the ray is finished.
+template <class T>
+__device__ __forceinline__ bool ray_step(const DevField& F, const TraceArgs& A, RayState& r, unsigned* err) {
+  // a ray that starts on or past its stop surface takes no step; afterwards only the
+  // shortened last step ends the ray (a full step that overshoots eta_stop is followed by
+  // a short step back onto the surface)
+  if (r.n_steps == 0 && !(r.y[3] > r.eta_stop)) return true;
+  if (r.n_steps >= A.max_steps) {
+    r.status = MT_RAY_MAX_STEPS;
+    return true;
+  }
+  const bool grav = A.gravity_on != 0;
+  double k[10], acc[10], t[10];
+  int lf = 0;
+  if (!geodesic_rhs<T>(F, grav, r.y, k, &lf, err)) {
+    r.status = MT_RAY_LEFT_DOMAIN;
+    return true;
+  }
+  const double k0 = r.y[4];
+  const double dxl = F.dx0 / (double)(1u << lf);
+  double h = dxl / ((double)A.steps_per_cell * fabs(k0));
+  bool last = false;
+  if (r.y[3] + k0 * h <= r.eta_stop) {
+    h = (r.eta_stop - r.y[3]) / k0;
+    last = true;
+  }
+  const double h2 = 0.5 * h, h3 = h / 3.0, h6 = h / 6.0;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    acc[i] = r.y[i] + h6 * k[i];
+    t[i] = r.y[i] + h2 * k[i];
+  }
+  if (!geodesic_rhs<T>(F, grav, t, k, nullptr, err)) {
+    r.status = MT_RAY_LEFT_DOMAIN;
+    return true;
+  }
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    acc[i] += h3 * k[i];
+    t[i] = r.y[i] + h2 * k[i];
+  }
+  if (!geodesic_rhs<T>(F, grav, t, k, nullptr, err)) {
+    r.status = MT_RAY_LEFT_DOMAIN;
+    return true;
+  }
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    acc[i] += h3 * k[i];
+    t[i] = r.y[i] + h * k[i];
+  }
+  if (!geodesic_rhs<T>(F, grav, t, k, nullptr, err)) {
+    r.status = MT_RAY_LEFT_DOMAIN;
+    return true;
+  }
+  bool finite = true;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    r.y[i] = acc[i] + h6 * k[i];
+    finite = finite && isfinite(r.y[i]);
+  }
+  r.lambda += h;
+  r.n_steps += 1;
+  if (!finite) {
+    r.status = MT_RAY_NONFINITE;
+    return true;
+  }
+  return last;
+}
+
+template <class T>
+__device__ void ray_finish(const DevField& F, const TraceArgs& A, const RayState& r, long long ray, long long n,
+                           const OutPtrs& O, unsigned* err) {
+  const double* y = r.y;
+  double a_s;
+  bg_eval(F, y[3], &a_s, nullptr);
+  double phi_s = 0.0;
+  int lev = -1;
+  double u[3];
+  if (r.status != MT_RAY_NONFINITE && coarse_coords<T>(F, y, u)) lev = locate_level(F, u, err);
+  if (A.gravity_on && r.status != MT_RAY_NONFINITE) {
+    T p, g[3], pe;
+    int l;
+    if (sample_field<T>(F, y, y[3], &p, g, &pe, &l, err)) phi_s = (double)p;
+  }
+  const double dx = y[0] - r.xo[0], dy = y[1] - r.xo[1], dz = y[2] - r.xo[2];
+  const double chi = sqrt(dx * dx + dy * dy + dz * dz);
+  const double z0 = 1.0 / a_s - 1.0;                                        // Eq. (23)
+  const double z1 = z0 + (r.phi_o - phi_s) / a_s;                           // Eq. (24)
+  const double z4 = z1 - 2.0 * y[8] / a_s;                                  // Eq. (27), v = 0
+  const double z5 = (a_s * fabs(y[4]) * (1.0 + phi_s)) / (1.0 + r.phi_o) - 1.0;  // Eq. (28), v = 0
+  if (O.x) {
+    O.x[ray] = y[0];
+    O.x[n + ray] = y[1];
+    O.x[2 * n + ray] = y[2];
+  }
+  if (O.k) {
+    O.k[ray] = y[4];
+    O.k[n + ray] = y[5];
+    O.k[2 * n + ray] = y[6];
+    O.k[3 * n + ray] = y[7];
+  }
+  if (O.eta) O.eta[ray] = y[3];
+  if (O.lambda) O.lambda[ray] = r.lambda;
+  if (O.chi) O.chi[ray] = chi;
+  if (O.path) O.path[ray] = y[9];
+  if (O.z0) O.z0[ray] = z0;
+  if (O.z1) O.z1[ray] = z1;
+  if (O.z4) O.z4[ray] = z4;
+  if (O.z5) O.z5[ray] = z5;
+  if (O.d_a) O.d_a[ray] = a_s * chi;
+  if (O.d_l) O.d_l[ray] = (1.0 + z5) * (1.0 + z5) * a_s * chi;
+  if (O.phi_o) O.phi_o[ray] = r.phi_o;
+  if (O.phi_s) O.phi_s[ray] = phi_s;
+  if (O.isw) O.isw[ray] = y[8];
+  if (O.n_steps) O.n_steps[ray] = r.n_steps;
+  if (O.level) O.level[ray] = lev;
+  if (O.status) O.status[ray] = r.status;
+}
+
+}  // namespace mt
