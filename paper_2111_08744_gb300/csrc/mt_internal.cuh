@@ -54,6 +54,14 @@ struct DevField {
   int pad;
   double bg_eta0, bg_deta, bg_inv_deta;
   double eta_o;     // observer time = last background node
+  // mixed-precision path: finest-level integer coordinates and single-precision tables
+  const float4* bgf;  // per node j: H_j, deta H'_j, H_{j+1}, deta H'_{j+1}
+  double inv_dxf;     // N_L / box (finest level cells per unit length)
+  int nf;             // N_L = N_0 2^L
+  float inv_dxf_f;    // N_L / box
+  float dx0_f;        // dx_0
+  float bg_inv_deta_f;
+  float inv_dseta[kMaxSlices];  // 1 / (eta_{s+1} - eta_s)
 };
 
 struct DevCones {
@@ -174,22 +182,14 @@ __device__ __forceinline__ int locate_level(const DevField& F, const double* u, 
   return lf;
 }
 
-// CIC (Eq. 8) at level l with the two bracketing slices s, s+1 (or slice 0 when S = 1):
+// CIC (Eq. 8) gather at level l around lower corner i0 (unwrapped level-l indices) with
+// in-cell fractions f, for the two bracketing slices s, s+1 (or slice 0 when S = 1):
 // out[0..3] at slice s, out[4..7] at slice s+1.  Returns false if a neighbour is absent.
 template <class T>
-__device__ __forceinline__ bool cic_level(const DevField& F, int l, const double* u, int s, T* out, unsigned* err) {
+__device__ __forceinline__ bool cic_gather(const DevField& F, int l, const long long* i0, const T* f, int s, T* out,
+                                          unsigned* err) {
   using V = typename Vec4<T>::type;
   const long long Nl = (long long)F.nc << l;
-  const double sc = (double)(1ll << l);
-  long long i0[3];
-  T f[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    double U = u[d] * sc - 0.5;
-    double fl = floor(U);
-    i0[d] = (long long)fl;
-    f[d] = (T)(U - fl);
-  }
   // wrapped corner coordinates a[d][c] for c = 0, 1
   unsigned a[3][2];
 #pragma unroll
@@ -205,31 +205,33 @@ __device__ __forceinline__ bool cic_level(const DevField& F, int l, const double
       a[d][c] = (unsigned)v;
     }
   }
-  long long rows[8];
+  // row indices fit 32 bits (level-0 rows < 2^31, octets < 2^28); addresses are formed in 64 bits
+  unsigned rows[8];
   if (l == 0) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) rows[c] = (long long)morton(a[0][c & 1], a[1][(c >> 1) & 1], a[2][(c >> 2) & 1]);
+    for (int c = 0; c < 8; ++c) rows[c] = (unsigned)morton(a[0][c & 1], a[1][(c >> 1) & 1], a[2][(c >> 2) & 1]);
   } else {
     // parents of the two corners per axis coincide iff the lower corner index is even
     const int ox = (int)(i0[0] & 1), oy = (int)(i0[1] & 1), oz = (int)(i0[2] & 1);
-    long long oct[8];
+    unsigned oct[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int qx = q & 1, qy = (q >> 1) & 1, qz = (q >> 2) & 1;
       if ((qx && !ox) || (qy && !oy) || (qz && !oz)) {
-        oct[q] = -1;
+        oct[q] = 0u;
         continue;
       }
       const unsigned long long pk = morton(a[0][qx] >> 1, a[1][qy] >> 1, a[2][qz] >> 1);
-      oct[q] = hash_find(F.hash[l], pk, err);
-      if (oct[q] < 0) return false;
+      const long long o = hash_find(F.hash[l], pk, err);
+      if (o < 0) return false;
+      oct[q] = (unsigned)o;
     }
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
       const int q = (ox ? cx : 0) | ((oy ? cy : 0) << 1) | ((oz ? cz : 0) << 2);
       const unsigned child = (a[0][cx] & 1u) | ((a[1][cy] & 1u) << 1) | ((a[2][cz] & 1u) << 2);
-      rows[c] = oct[q] * 8 + (long long)child;
+      rows[c] = oct[q] * 8u + child;
     }
   }
   const V* rec = (const V*)F.rec[l];
@@ -243,8 +245,9 @@ __device__ __forceinline__ bool cic_level(const DevField& F, int l, const double
     const T wy = (c & 2) ? f[1] : (T)1 - f[1];
     const T wz = (c & 4) ? f[2] : (T)1 - f[2];
     const T w = wx * wy * wz;
-    const V r0 = ldg4(&rec[rows[c] * S + s]);
-    const V r1 = ldg4(&rec[rows[c] * S + s1]);
+    const V* rc = rec + (size_t)rows[c] * (size_t)S;
+    const V r0 = ldg4(rc + s);
+    const V r1 = ldg4(rc + s1);
     out[0] += w * r0.x;
     out[1] += w * r0.y;
     out[2] += w * r0.z;
@@ -255,6 +258,22 @@ __device__ __forceinline__ bool cic_level(const DevField& F, int l, const double
     out[7] += w * r1.w;
   }
   return true;
+}
+
+// CIC at level l from coarse-cell coordinates u: i0 = floor(u 2^l - 1/2), f = remainder.
+template <class T>
+__device__ __forceinline__ bool cic_level(const DevField& F, int l, const double* u, int s, T* out, unsigned* err) {
+  const double sc = (double)(1ll << l);
+  long long i0[3];
+  T f[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double U = u[d] * sc - 0.5;
+    double fl = floor(U);
+    i0[d] = (long long)fl;
+    f[d] = (T)(U - fl);
+  }
+  return cic_gather<T>(F, l, i0, f, s, out, err);
 }
 
 // Field at (x, eta): phi, grad phi and d phi/d eta, with the level fallback of Sect. 2.2
@@ -308,6 +327,7 @@ struct mt_octree {
   ulonglong2* hash_alloc[mt::kMaxLevels + 1];
   int64_t count[mt::kMaxLevels + 1];
   double* bg_dev;
+  float4* bgf_dev;
   double* bg_host;
   int bg_n;
   unsigned long long* ws;  // [0] ray queue counter, [1] error flags

@@ -1,0 +1,276 @@
+// Mixed-precision RK4 step (FP32 field and arithmetic inside a step, FP64 ray state).
+//
+// Same method as the FP64 step (Sect. 2.2: RK4 in lambda, N steps per AMR cell, CIC with
+// level fallback, Eqs. 2-4), arranged so that double precision is spent only where it
+// carries accuracy:
+//   * at the step start the FP64 position is split once into an integer cell index on the
+//     finest level plus an FP32 in-cell fraction; stage positions are FP32 offsets from it,
+//     so locate and CIC run on integers and floats only;
+//   * the background H(eta) is a single-precision Hermite interpolant around the step's
+//     table node; the time slices are bracketed by FP32 offsets from the step start;
+//   * the right-hand side of Eqs. (2)-(4) is evaluated in FP32 at FP32 stage states
+//     (its rounding enters the state only through h * derivative);
+//   * the state update y += h sum_i b_i K_i stays FP64: x and eta advance by h k(step
+//     start) in FP64 plus an FP32 correction from the stage offsets of k.
+#pragma once
+
+#include "mt_internal.cuh"
+
+namespace mt {
+
+// Finest-level integer index and FP32 fraction of an FP64 position (once per step).
+__device__ __forceinline__ bool finest_base(const DevField& F, const double* x, int* ib, float* fb) {
+  const double nf = (double)F.nf;
+  bool inside = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double v = x[d] * F.inv_dxf;
+    if (F.periodic) {
+      v = v - nf * floor(v * (1.0 / nf));
+    } else {
+      inside = inside && (v >= 0.0) && (v < nf);
+    }
+    const double fl = floor(v);
+    ib[d] = (int)fl;
+    fb[d] = (float)(v - fl);
+  }
+  return inside;
+}
+
+// Stage position: base index + (fraction + offset) in finest cells.
+__device__ __forceinline__ bool stage_coords(const DevField& F, const int* ib, const float* fb, const float* offx,
+                                             int* ic, float* fc) {
+  bool inside = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float U = fb[d] + offx[d] * F.inv_dxf_f;
+    const float c = floorf(U);
+    int i = ib[d] + (int)c;
+    fc[d] = U - c;
+    if (F.periodic) {
+      i &= (F.nf - 1);
+    } else {
+      inside = inside && (i >= 0) && (i < F.nf);
+    }
+    ic[d] = i;
+  }
+  return inside;
+}
+
+// Most refined level containing the finest cell ic (hash probe of each level's parent).
+__device__ __forceinline__ int locate_level_int(const DevField& F, const int* ic, unsigned* err) {
+  int lf = 0;
+  for (int l = 1; l <= F.L; ++l) {
+    const int sh = F.L - l + 1;
+    const unsigned long long pk = morton((unsigned)ic[0] >> sh, (unsigned)ic[1] >> sh, (unsigned)ic[2] >> sh);
+    if (hash_find(F.hash[l], pk, err) < 0) break;
+    lf = l;
+  }
+  return lf;
+}
+
+// CIC with level fallback from level lfin, FP32; v as in cic_gather.
+__device__ __forceinline__ bool sample_int(const DevField& F, const int* ic, const float* fc, int lfin, int s, float* v,
+                                           unsigned* err) {
+  for (int l = lfin; l >= 0; --l) {
+    const int sh = F.L - l;
+    const float inv = 1.0f / (float)(1 << sh);
+    long long i0[3];
+    float f[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int ilev = ic[d] >> sh;
+      const float fl = ((float)(ic[d] & ((1 << sh) - 1)) + fc[d]) * inv;  // fraction in the level-l cell
+      if (fl >= 0.5f) {
+        i0[d] = ilev;
+        f[d] = fl - 0.5f;
+      } else {
+        i0[d] = (long long)ilev - 1;
+        f[d] = fl + 0.5f;
+      }
+    }
+    if (cic_gather<float>(F, l, i0, f, s, v, err)) return true;
+  }
+  return false;
+}
+
+struct MixedStep {
+  int ib[3];
+  float fb[3];
+  int jb;        // background node of the step start
+  float tb;      // fractional node coordinate of the step start
+  int sb;        // slice bracket at the step start
+  float e_lo;    // eta_step - eta_{sb}
+  float e_hi;    // eta_step - eta_{sb+1}
+};
+
+// FP32 right-hand side of Eqs. (2)-(4) at the stage with offsets (offx, offe) from the step
+// start and wave vector (k0, k).  *lf (if non-null) receives the most refined level.
+__device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const MixedStep& B, double eta_step,
+                                          const float* offx, float offe, float k0, const float* k, float* Kk0,
+                                          float* Kk, float* KI, float* Ks, int* lf, unsigned* err) {
+  // background H(eta_step + offe)
+  const float t = B.tb + offe * F.bg_inv_deta_f;
+  const float ct = floorf(t);
+  int j = B.jb + (int)ct;
+  float ft = t - ct;
+  if (j < 0) {
+    ft += (float)j;
+    j = 0;
+  } else if (j > F.bg_n - 2) {
+    ft += (float)(j - (F.bg_n - 2));
+    j = F.bg_n - 2;
+  }
+  const float4 p = __ldg(&F.bgf[j]);
+  const float t2 = ft * ft, t3 = t2 * ft;
+  const float H = (2.0f * t3 - 3.0f * t2 + 1.0f) * p.x + (t3 - 2.0f * t2 + ft) * p.y + (-2.0f * t3 + 3.0f * t2) * p.z +
+                  (t3 - t2) * p.w;
+  float phi = 0.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, pe = 0.0f;
+  if (grav || lf) {
+    int ic[3];
+    float fc[3];
+    if (!stage_coords(F, B.ib, B.fb, offx, ic, fc)) return false;
+    const int l = locate_level_int(F, ic, err);
+    if (lf) *lf = l;
+    if (grav) {
+      int s = B.sb;
+      float es = B.e_lo;  // eta_stage - eta_s = es + offe
+      if (F.S > 1) {
+        const bool below = (s > 0) && (B.e_lo + offe < 0.0f);
+        const bool above = (s < F.S - 2) && (B.e_hi + offe >= 0.0f);
+        if (below || above) {  // the stage left the step's slice bracket (rare): re-bracket in FP64
+          const double e = eta_step + (double)offe;
+          s = 0;
+          while (s < F.S - 2 && F.seta[s + 1] <= e) ++s;
+          es = (float)(eta_step - F.seta[s]);
+        }
+      }
+      float v[8];
+      if (!sample_int(F, ic, fc, l, s, v, err)) return false;
+      if (F.S == 1) {
+        phi = v[0];
+        g0 = v[1];
+        g1 = v[2];
+        g2 = v[3];
+      } else {
+        const float ids = F.inv_dseta[s];
+        const float w = (es + offe) * ids;
+        phi = v[0] + w * (v[4] - v[0]);
+        g0 = v[1] + w * (v[5] - v[1]);
+        g1 = v[2] + w * (v[6] - v[2]);
+        g2 = v[3] + w * (v[7] - v[3]);
+        pe = (v[4] - v[0]) * ids;
+      }
+    }
+  }
+  (void)phi;
+  const float dphidl = g0 * k[0] + g1 * k[1] + g2 * k[2] + pe * k0;
+  const float k00 = k0 * k0;
+  const float bg = -2.0f * H * k0;
+  *Kk0 = bg * k0 - 2.0f * dphidl * k0 + 2.0f * pe * k00;
+  Kk[0] = bg * k[0] + 2.0f * dphidl * k[0] - 2.0f * g0 * k00;
+  Kk[1] = bg * k[1] + 2.0f * dphidl * k[1] - 2.0f * g1 * k00;
+  Kk[2] = bg * k[2] + 2.0f * dphidl * k[2] - 2.0f * g2 * k00;
+  *KI = -pe * k0;
+  *Ks = sqrtf(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+  return true;
+}
+
+// One mixed-precision RK4 step; state and status conventions as ray_step.
+template <class RayStateT, class TraceArgsT>
+__device__ bool ray_step_mixed(const DevField& F, const TraceArgsT& A, RayStateT& r, unsigned* err) {
+  if (r.n_steps == 0 && !(r.y[3] > r.eta_stop)) return true;
+  if (r.n_steps >= A.max_steps) {
+    r.status = MT_RAY_MAX_STEPS;
+    return true;
+  }
+  const bool grav = A.gravity_on != 0;
+  MixedStep B;
+  if (!finest_base(F, r.y, B.ib, B.fb)) {
+    r.status = MT_RAY_LEFT_DOMAIN;
+    return true;
+  }
+  const double eta = r.y[3];
+  {
+    const double t0 = (eta - F.bg_eta0) * F.bg_inv_deta;
+    const double jf = floor(t0);
+    B.jb = (int)jf;
+    B.tb = (float)(t0 - jf);
+    int s = 0;
+    while (s < F.S - 2 && F.seta[s + 1] <= eta) ++s;
+    B.sb = s;
+    B.e_lo = (float)(eta - F.seta[s]);
+    B.e_hi = F.S > 1 ? (float)(eta - F.seta[s + 1]) : 0.0f;
+  }
+  const float k0s = (float)r.y[4];
+  const float ks[3] = {(float)r.y[5], (float)r.y[6], (float)r.y[7]};
+  // stage offsets (from the step start) and weighted sums of the stage derivatives
+  float offx[3] = {0.0f, 0.0f, 0.0f}, offe = 0.0f, offk0 = 0.0f, offk[3] = {0.0f, 0.0f, 0.0f};
+  float sx[3] = {0.0f, 0.0f, 0.0f}, se = 0.0f, sk0 = 0.0f, sk[3] = {0.0f, 0.0f, 0.0f}, sI = 0.0f, ss = 0.0f;
+  float h = 0.0f;
+  bool last = false;
+#pragma unroll 1
+  for (int st = 0; st < 4; ++st) {
+    const float kst0 = k0s + offk0;
+    const float kst[3] = {ks[0] + offk[0], ks[1] + offk[1], ks[2] + offk[2]};
+    float Kk0, Kk[3], KI, Ks;
+    int lf = 0;
+    if (!rhs_mixed(F, grav, B, eta, offx, offe, kst0, kst, &Kk0, Kk, &KI, &Ks, st == 0 ? &lf : nullptr, err)) {
+      r.status = MT_RAY_LEFT_DOMAIN;
+      return true;
+    }
+    if (st == 0) {
+      const float dxl = F.dx0_f / (float)(1 << lf);
+      h = dxl / ((float)A.steps_per_cell * fabsf(k0s));
+      const float d = (float)(r.eta_stop - eta);
+      if (k0s * h <= d) {
+        h = d / k0s;
+        last = true;
+      }
+    }
+    const float b = (st == 0 || st == 3) ? (1.0f / 6.0f) : (1.0f / 3.0f);
+    sk0 += b * Kk0;
+    sk[0] += b * Kk[0];
+    sk[1] += b * Kk[1];
+    sk[2] += b * Kk[2];
+    sI += b * KI;
+    ss += b * Ks;
+    se += b * offk0;
+    sx[0] += b * offk[0];
+    sx[1] += b * offk[1];
+    sx[2] += b * offk[2];
+    const float c = (st == 2 ? 1.0f : 0.5f) * h;  // next stage at y + c K
+    offx[0] = c * kst[0];
+    offx[1] = c * kst[1];
+    offx[2] = c * kst[2];
+    offe = c * kst0;
+    offk0 = c * Kk0;
+    offk[0] = c * Kk[0];
+    offk[1] = c * Kk[1];
+    offk[2] = c * Kk[2];
+  }
+  const double hd = (double)h;
+  bool finite = true;
+  // positions and eta: h k(step start) in FP64 plus the FP32 stage corrections
+  r.y[0] += hd * r.y[5] + (double)(h * sx[0]);
+  r.y[1] += hd * r.y[6] + (double)(h * sx[1]);
+  r.y[2] += hd * r.y[7] + (double)(h * sx[2]);
+  r.y[3] += hd * r.y[4] + (double)(h * se);
+  r.y[4] += (double)(h * sk0);
+  r.y[5] += (double)(h * sk[0]);
+  r.y[6] += (double)(h * sk[1]);
+  r.y[7] += (double)(h * sk[2]);
+  r.y[8] += (double)(h * sI);
+  r.y[9] += (double)(h * ss);
+#pragma unroll
+  for (int i = 0; i < 10; ++i) finite = finite && isfinite(r.y[i]);
+  r.lambda += hd;
+  r.n_steps += 1;
+  if (!finite) {
+    r.status = MT_RAY_NONFINITE;
+    return true;
+  }
+  return last;
+}
+
+}  // namespace mt

@@ -76,6 +76,7 @@ void release(mt_octree* t) {
     if (t->hash_alloc[l]) cudaFree(t->hash_alloc[l]);
   }
   if (t->bg_dev) cudaFree(t->bg_dev);
+  if (t->bgf_dev) cudaFree(t->bgf_dev);
   if (t->ws) cudaFree(t->ws);
   std::free(t->bg_host);
   if (prev >= 0) cudaSetDevice(prev);
@@ -218,6 +219,33 @@ extern "C" mt_status mt_build_octree(const mt_grid_desc* grid, const mt_level_da
   F.bg_deta = de;
   F.bg_inv_deta = 1.0 / de;
   F.eta_o = bg_table[4 * (bg_n - 1)];
+  {
+    // single-precision Hermite table of H(eta) for the mixed path: node pairs (j, j+1)
+    float* hf = (float*)std::malloc(sizeof(float) * 4 * bg_n);
+    if (!hf) {
+      st = MT_ERR_OOM;
+      goto fail;
+    }
+    for (int j = 0; j < bg_n; ++j) {
+      const int q = j + 1 < bg_n ? j + 1 : j;
+      hf[4 * j + 0] = (float)bg_table[4 * j + 2];
+      hf[4 * j + 1] = (float)(de * bg_table[4 * j + 3]);
+      hf[4 * j + 2] = (float)bg_table[4 * q + 2];
+      hf[4 * j + 3] = (float)(de * bg_table[4 * q + 3]);
+    }
+    cudaError_t e1 = cudaMalloc(&t->bgf_dev, sizeof(float4) * bg_n);
+    if (e1 == cudaSuccess) e1 = cudaMemcpy(t->bgf_dev, hf, sizeof(float4) * bg_n, cudaMemcpyHostToDevice);
+    std::free(hf);
+    MT_TRY(e1);
+    t->device_bytes += sizeof(float4) * bg_n;
+  }
+  F.bgf = t->bgf_dev;
+  F.nf = nc << L;
+  F.inv_dxf = (double)F.nf / grid->box;
+  F.inv_dxf_f = (float)F.inv_dxf;
+  F.dx0_f = (float)F.dx0;
+  F.bg_inv_deta_f = (float)(1.0 / de);
+  for (int s = 0; s + 1 < S; ++s) F.inv_dseta[s] = (float)(1.0 / (grid->slice_eta[s + 1] - grid->slice_eta[s]));
 
   for (int l = 0; l <= L; ++l) {
     const long long n = levels[l].count;

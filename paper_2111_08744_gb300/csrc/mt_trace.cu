@@ -21,11 +21,11 @@ __device__ void ray_init(const DevField& F, const DevCones& C, const double* __r
                          long long ray, bool grav, RayState& r, unsigned* err) {
   int c = 0;
   while (c + 1 < C.n && C.begin[c + 1] <= ray) ++c;
-  ray_start<T>(F, C.obs[c], C.eta_stop[c], dirs, n, ray, grav, r, err);
+  r = ray_start<T>(F, C.obs[c], C.eta_stop[c], dirs, n, ray, grav, err);
 }
 
 template <class T>
-__global__ void __launch_bounds__(kBlock) trace_kernel(DevField F, DevCones C, const double* __restrict__ dirs,
+__global__ void __launch_bounds__(kBlock, 4) trace_kernel(DevField F, DevCones C, const double* __restrict__ dirs,
                                                        OutPtrs O, TraceArgs A, unsigned long long* ws) {
   unsigned* err = (unsigned*)(ws + 1);
   const unsigned lane = threadIdx.x & 31u;

@@ -13,6 +13,7 @@
 #include <cstdint>
 
 #include "mt_internal.cuh"
+#include "mt_mixed.cuh"
 
 namespace mt {
 
@@ -89,8 +90,10 @@ struct RayState {
 // Initial state of a ray leaving observer xo at eta_o along dirs[:, ray] (Sect. 2.2):
 // k0 = -1 and k^i = n sqrt((1 + 2 phi_o)/(1 - 2 phi_o)) (null condition of Eq. 1).
 template <class T>
-__device__ void ray_start(const DevField& F, const double* xo, double eta_stop, const double* __restrict__ dirs,
-                          long long n, long long ray, bool grav, RayState& r, unsigned* err) {
+__device__ __noinline__ RayState ray_start(const DevField& F, const double* xo, double eta_stop,
+                                           const double* __restrict__ dirs, long long n, long long ray, bool grav,
+                                           unsigned* err) {
+  RayState r;
   r.xo[0] = xo[0];
   r.xo[1] = xo[1];
   r.xo[2] = xo[2];
@@ -116,11 +119,13 @@ __device__ void ray_start(const DevField& F, const double* xo, double eta_stop, 
   r.phi_o = phi_o;
   r.n_steps = 0;
   r.status = MT_RAY_OK;
+  return r;
 }
 
 // One RK4 step (Sect. 2.2).  Returns true when the ray is finished.
 template <class T>
 __device__ __forceinline__ bool ray_step(const DevField& F, const TraceArgs& A, RayState& r, unsigned* err) {
+  if constexpr (sizeof(T) == 4) return ray_step_mixed(F, A, r, err);
   // a ray that starts on or past its stop surface takes no step; afterwards only the
   // shortened last step ends the ray (a full step that overshoots eta_stop is followed by
   // a short step back onto the surface)
@@ -188,7 +193,7 @@ __device__ __forceinline__ bool ray_step(const DevField& F, const TraceArgs& A, 
 }
 
 template <class T>
-__device__ void ray_finish(const DevField& F, const TraceArgs& A, const RayState& r, long long ray, long long n,
+__device__ __noinline__ void ray_finish(const DevField& F, const TraceArgs& A, const RayState r, long long ray, long long n,
                            const OutPtrs& O, unsigned* err) {
   const double* y = r.y;
   double a_s;

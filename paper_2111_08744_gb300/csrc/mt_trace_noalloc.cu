@@ -38,7 +38,7 @@ unsigned long long* g_scratch_addr[kMaxDevices];  // device address of g_noalloc
 unsigned long long g_host_table[kScratchWords - kHeaderWords];  // staging of the cone table (host)
 
 template <class T>
-__global__ void __launch_bounds__(kBlock) trace_kernel_noalloc(DevField F, int n_cones, const double* __restrict__ dirs,
+__global__ void __launch_bounds__(kBlock, 4) trace_kernel_noalloc(DevField F, int n_cones, const double* __restrict__ dirs,
                                                                OutPtrs O, TraceArgs A, unsigned long long* scratch,
                                                                unsigned* err) {
   const long long* begin = (const long long*)(scratch + kBeginOff);
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kBlock) trace_kernel_noalloc(DevField F, int n
             const int mid = (lo + hi) >> 1;
             if (begin[mid] <= ray) lo = mid; else hi = mid;
           }
-          ray_start<T>(F, obs + 3 * lo, stop[lo], dirs, n, ray, grav, r, err);
+          r = ray_start<T>(F, obs + 3 * lo, stop[lo], dirs, n, ray, grav, err);
         } else {
           exhausted = true;
         }
