@@ -184,6 +184,39 @@ mt_status mt_trace_rays(const mt_octree* tree, const mt_trace_params* params, co
                         const mt_ray_out* out, void* stream);
 
 /*
+ * mt_trace_rays_adjoint -- derivatives of the ray map (Sect. 2.3 distortion matrix, and the
+ * gradient of a loss on the end points with respect to the gridded potential).
+ *
+ * The end point of a ray is taken on its iso-eta stop surface:
+ *     xi = x - (k / k0) (eta - eta_stop).
+ * Forward mode (jac or lens non-NULL): two tangents of the FP64 RK4 map along the observer's
+ * screen vectors e_1 = (-sin t1, cos t1, 0), e_2 = (-cos t1 cos t2, -sin t1 cos t2, sin t2)
+ * (t1, t2 the azimuth and polar angle of the direction; Sect. 2.3.2) give
+ *     A_ab = (d xi / d theta_b) . e~_a / chi,   chi = |xi - x_o|,
+ * with e~ the beta-screen of the end point (Eq. 21 in the limit of an infinitesimal beam,
+ * without neighbouring rays).  jac: device [4][N] = A11, A12, A21, A22.  lens: device
+ * [5][N] = kappa, gamma_1, gamma_2, omega, det A (= 1/mu) from Eq. (11).  Asynchronous.
+ *
+ * Reverse mode (dL_dxi and dL_drec non-NULL): given dL/dxi (device [3][N]), ACCUMULATES
+ * (+=) dL/d(record) into dL_drec[l] (device FP64 buffers [count_l][n_slices][4], one per
+ * level 0..n_levels, same layout as the records; a NULL entry skips that level), through the
+ * exact adjoint of the discrete map (RK4 stages, CIC weights, time slices, step-size and
+ * last-step dependence, and phi at the observer).  States are checkpointed every
+ * checkpoint_every (1..64) steps and each segment is recomputed.  Synchronous: the call
+ * counts each ray's steps, allocates a temporary checkpoint buffer (8 doubles per
+ * checkpoint), runs the sweep and frees it.  Rays that do not end with MT_RAY_OK add nothing.
+ *
+ * Both modes integrate the ray in FP64 arithmetic (records of the octree's precision) and
+ * write the ray outputs `out` (NULL pointers skip an output) of that integration.
+ * Errors: as mt_trace_rays; MT_ERR_INVALID_ARG if neither mode is requested or reverse-mode
+ * arguments are incomplete; MT_ERR_OOM if the checkpoint buffer cannot be allocated.
+ */
+mt_status mt_trace_rays_adjoint(const mt_octree* tree, const mt_trace_params* params, const double* dirs,
+                                int64_t n_rays, const mt_ray_out* out, double* jac, double* lens,
+                                const double* dL_dxi, double* const* dL_drec, int32_t checkpoint_every,
+                                void* stream);
+
+/*
  * mt_trace_rays_noalloc -- the same trace as mt_trace_rays, for callers that must not
  * allocate GPU memory.  The paper has no counterpart: this is a property of this
  * library's interface, not of the method.

@@ -76,6 +76,10 @@ def load():
         lib.mt_trace_rays.restype = ctypes.c_int
         lib.mt_trace_rays.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64,
                                       ctypes.POINTER(mt_ray_out), P]
+        lib.mt_trace_rays_adjoint.restype = ctypes.c_int
+        lib.mt_trace_rays_adjoint.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64,
+                                              ctypes.POINTER(mt_ray_out), P, P, P, ctypes.POINTER(P),
+                                              ctypes.c_int32, P]
         lib.mt_trace_rays_noalloc.restype = ctypes.c_int
         lib.mt_trace_rays_noalloc.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64,
                                               ctypes.POINTER(mt_ray_out), P]
@@ -125,6 +129,11 @@ def mt_build_octree(grid, levels, bg_table, bg_n, stream, out):
 
 def mt_trace_rays(tree, params, dirs, n_rays, out, stream):
     return load().mt_trace_rays(tree, params, dirs, n_rays, out, stream)
+
+
+def mt_trace_rays_adjoint(tree, params, dirs, n_rays, out, jac, lens, dL_dxi, dL_drec, checkpoint_every, stream):
+    return load().mt_trace_rays_adjoint(tree, params, dirs, n_rays, out, jac, lens, dL_dxi, dL_drec,
+                                        checkpoint_every, stream)
 
 
 def mt_trace_rays_noalloc(tree, params, dirs, n_rays, out, stream):
@@ -273,3 +282,41 @@ def trace_rays(tree: Octree, params: TraceParams, dirs, out=None, stream=None):
                                 _stream_handle(stream))
     _check(code, "mt_trace_rays")
     return out
+
+
+def trace_rays_adjoint(tree: Octree, params: TraceParams, dirs, jacobian=True, lensing=True, dL_dxi=None,
+                       checkpoint_every=64, out=None, dL_drec=None, stream=None):
+    """mt_trace_rays_adjoint on CUDA tensors.
+
+    Returns the ray outputs plus "jac" [4, N] and "lens" [5, N] (forward mode) and, when dL_dxi
+    ([3, N] float64 CUDA) is given, "dL_drec": one float64 tensor per level shaped like that
+    level's records [count, n_slices, 4] (accumulated into `dL_drec` if passed).
+    """
+    torch = _require_cuda()
+    n = int(dirs.shape[1])
+    if out is None:
+        out = alloc_outputs(n, dirs.device)
+    jac = torch.empty((4, n), dtype=torch.float64, device=dirs.device) if jacobian else None
+    lens = torch.empty((5, n), dtype=torch.float64, device=dirs.device) if lensing else None
+    arr = None
+    if dL_dxi is not None:
+        if dL_drec is None:
+            cells, _ = tree.info()
+            dL_drec = [torch.zeros((c, tree.n_slices, 4), dtype=torch.float64, device=dirs.device) for c in cells]
+        arr = (ctypes.c_void_p * len(dL_drec))(*[t.data_ptr() if t.numel() else None for t in dL_drec])
+        dL_dxi = dL_dxi.contiguous()
+    o = ray_out_struct(out)
+    code = load().mt_trace_rays_adjoint(tree.handle, ctypes.byref(params.c), dirs.data_ptr(), n, ctypes.byref(o),
+                                        jac.data_ptr() if jac is not None else None,
+                                        lens.data_ptr() if lens is not None else None,
+                                        dL_dxi.data_ptr() if dL_dxi is not None else None, arr,
+                                        int(checkpoint_every), _stream_handle(stream))
+    _check(code, "mt_trace_rays_adjoint")
+    res = dict(out)
+    if jac is not None:
+        res["jac"] = jac
+    if lens is not None:
+        res["lens"] = lens
+    if dL_dxi is not None:
+        res["dL_drec"] = dL_drec
+    return res

@@ -182,13 +182,11 @@ __device__ __forceinline__ int locate_level(const DevField& F, const double* u, 
   return lf;
 }
 
-// CIC (Eq. 8) gather at level l around lower corner i0 (unwrapped level-l indices) with
-// in-cell fractions f, for the two bracketing slices s, s+1 (or slice 0 when S = 1):
-// out[0..3] at slice s, out[4..7] at slice s+1.  Returns false if a neighbour is absent.
-template <class T>
-__device__ __forceinline__ bool cic_gather(const DevField& F, int l, const long long* i0, const T* f, int s, T* out,
-                                          unsigned* err) {
-  using V = typename Vec4<T>::type;
+// Rows of the 8 CIC neighbours at level l around lower corner i0 (unwrapped level-l indices),
+// corner c = (c & 1, (c >> 1) & 1, (c >> 2) & 1).  Returns false if a neighbour is absent.
+// Row indices fit 32 bits (level-0 rows < 2^31, octets < 2^28); addresses are formed in 64 bits.
+__device__ __forceinline__ bool cic_rows(const DevField& F, int l, const long long* i0, unsigned* rows,
+                                         unsigned* err) {
   const long long Nl = (long long)F.nc << l;
   // wrapped corner coordinates a[d][c] for c = 0, 1
   unsigned a[3][2];
@@ -205,35 +203,45 @@ __device__ __forceinline__ bool cic_gather(const DevField& F, int l, const long 
       a[d][c] = (unsigned)v;
     }
   }
-  // row indices fit 32 bits (level-0 rows < 2^31, octets < 2^28); addresses are formed in 64 bits
-  unsigned rows[8];
   if (l == 0) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) rows[c] = (unsigned)morton(a[0][c & 1], a[1][(c >> 1) & 1], a[2][(c >> 2) & 1]);
-  } else {
-    // parents of the two corners per axis coincide iff the lower corner index is even
-    const int ox = (int)(i0[0] & 1), oy = (int)(i0[1] & 1), oz = (int)(i0[2] & 1);
-    unsigned oct[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int qx = q & 1, qy = (q >> 1) & 1, qz = (q >> 2) & 1;
-      if ((qx && !ox) || (qy && !oy) || (qz && !oz)) {
-        oct[q] = 0u;
-        continue;
-      }
-      const unsigned long long pk = morton(a[0][qx] >> 1, a[1][qy] >> 1, a[2][qz] >> 1);
-      const long long o = hash_find(F.hash[l], pk, err);
-      if (o < 0) return false;
-      oct[q] = (unsigned)o;
-    }
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
-      const int q = (ox ? cx : 0) | ((oy ? cy : 0) << 1) | ((oz ? cz : 0) << 2);
-      const unsigned child = (a[0][cx] & 1u) | ((a[1][cy] & 1u) << 1) | ((a[2][cz] & 1u) << 2);
-      rows[c] = oct[q] * 8u + child;
-    }
+    return true;
   }
+  // parents of the two corners per axis coincide iff the lower corner index is even
+  const int ox = (int)(i0[0] & 1), oy = (int)(i0[1] & 1), oz = (int)(i0[2] & 1);
+  unsigned oct[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int qx = q & 1, qy = (q >> 1) & 1, qz = (q >> 2) & 1;
+    if ((qx && !ox) || (qy && !oy) || (qz && !oz)) {
+      oct[q] = 0u;
+      continue;
+    }
+    const unsigned long long pk = morton(a[0][qx] >> 1, a[1][qy] >> 1, a[2][qz] >> 1);
+    const long long o = hash_find(F.hash[l], pk, err);
+    if (o < 0) return false;
+    oct[q] = (unsigned)o;
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+    const int q = (ox ? cx : 0) | ((oy ? cy : 0) << 1) | ((oz ? cz : 0) << 2);
+    const unsigned child = (a[0][cx] & 1u) | ((a[1][cy] & 1u) << 1) | ((a[2][cz] & 1u) << 2);
+    rows[c] = oct[q] * 8u + child;
+  }
+  return true;
+}
+
+// CIC (Eq. 8) gather at level l around lower corner i0 with in-cell fractions f, for the
+// two bracketing slices s, s+1 (or slice 0 when S = 1): out[0..3] at slice s, out[4..7] at
+// slice s+1.  Returns false if a neighbour is absent.
+template <class T>
+__device__ __forceinline__ bool cic_gather(const DevField& F, int l, const long long* i0, const T* f, int s, T* out,
+                                          unsigned* err) {
+  using V = typename Vec4<T>::type;
+  unsigned rows[8];
+  if (!cic_rows(F, l, i0, rows, err)) return false;
   const V* rec = (const V*)F.rec[l];
   const int S = F.S;
   const int s1 = (S > 1) ? s + 1 : s;

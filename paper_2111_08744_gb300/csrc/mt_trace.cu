@@ -78,9 +78,9 @@ int blocks_per_sm() {
 
 using namespace mt;
 
-namespace {
+namespace mt {
 
-mt_status check_params(const mt_trace_params* p, int64_t n_rays) {
+mt_status check_trace_params(const mt_trace_params* p, int64_t n_rays) {
   if (!p || n_rays < 0) return MT_ERR_INVALID_ARG;
   if (p->n_cones < 1 || p->n_cones > kMaxCones || p->steps_per_cell < 1 || p->max_steps < 1) return MT_ERR_INVALID_ARG;
   if (!p->observer || !p->z_max || !p->ray_begin) return MT_ERR_INVALID_ARG;
@@ -94,12 +94,23 @@ mt_status check_params(const mt_trace_params* p, int64_t n_rays) {
   return MT_OK;
 }
 
-}  // namespace
+void fill_cones(const mt_octree* tree, const mt_trace_params* params, DevCones* C) {
+  C->n = params->n_cones;
+  C->pad = 0;
+  for (int c = 0; c < C->n; ++c) {
+    C->begin[c] = params->ray_begin[c];
+    for (int d = 0; d < 3; ++d) C->obs[c][d] = params->observer[3 * c + d];
+    C->eta_stop[c] = host_eta_stop(tree, params->z_max[c]);
+  }
+  C->begin[C->n] = params->ray_begin[C->n];
+}
+
+}  // namespace mt
 
 extern "C" mt_status mt_trace_rays(const mt_octree* tree, const mt_trace_params* params, const double* dirs,
                                    int64_t n_rays, const mt_ray_out* out, void* stream_) {
   if (!tree || !out) return MT_ERR_INVALID_ARG;
-  mt_status st = check_params(params, n_rays);
+  mt_status st = check_trace_params(params, n_rays);
   if (st != MT_OK) return st;
   if (n_rays > 0 && !dirs) return MT_ERR_INVALID_ARG;
   if (n_rays == 0) return MT_OK;
@@ -108,14 +119,7 @@ extern "C" mt_status mt_trace_rays(const mt_octree* tree, const mt_trace_params*
   if (prev != tree->device && cudaSetDevice(tree->device) != cudaSuccess) return MT_ERR_CUDA;
   cudaStream_t stream = (cudaStream_t)stream_;
   DevCones C;
-  C.n = params->n_cones;
-  C.pad = 0;
-  for (int c = 0; c < C.n; ++c) {
-    C.begin[c] = params->ray_begin[c];
-    for (int d = 0; d < 3; ++d) C.obs[c][d] = params->observer[3 * c + d];
-    C.eta_stop[c] = host_eta_stop(tree, params->z_max[c]);
-  }
-  C.begin[C.n] = params->ray_begin[C.n];
+  fill_cones(tree, params, &C);
   OutPtrs O = {out->x, out->k, out->eta, out->lambda, out->chi, out->path, out->z0, out->z1, out->z4, out->z5,
                out->d_a, out->d_l, out->phi_o, out->phi_s, out->isw, out->n_steps, out->level, out->status};
   TraceArgs A;

@@ -123,9 +123,10 @@ __device__ __noinline__ RayState ray_start(const DevField& F, const double* xo, 
 }
 
 // One RK4 step (Sect. 2.2).  Returns true when the ray is finished.
+// One RK4 step in FP64 arithmetic with T-precision field records.  Returns true when the ray
+// is finished.
 template <class T>
-__device__ __forceinline__ bool ray_step(const DevField& F, const TraceArgs& A, RayState& r, unsigned* err) {
-  if constexpr (sizeof(T) == 4) return ray_step_mixed(F, A, r, err);
+__device__ __forceinline__ bool ray_step_fp64(const DevField& F, const TraceArgs& A, RayState& r, unsigned* err) {
   // a ray that starts on or past its stop surface takes no step; afterwards only the
   // shortened last step ends the ray (a full step that overshoots eta_stop is followed by
   // a short step back onto the surface)
@@ -192,6 +193,17 @@ __device__ __forceinline__ bool ray_step(const DevField& F, const TraceArgs& A, 
   return last;
 }
 
+// One RK4 step of the trace kernels: FP64 fields integrate in FP64; FP32 fields use the
+// mixed-precision step (mt_mixed.cuh).
+template <class T>
+__device__ __forceinline__ bool ray_step(const DevField& F, const TraceArgs& A, RayState& r, unsigned* err) {
+  if constexpr (sizeof(T) == 4) {
+    return ray_step_mixed(F, A, r, err);
+  } else {
+    return ray_step_fp64<T>(F, A, r, err);
+  }
+}
+
 template <class T>
 __device__ __noinline__ void ray_finish(const DevField& F, const TraceArgs& A, const RayState r, long long ray, long long n,
                            const OutPtrs& O, unsigned* err) {
@@ -241,5 +253,13 @@ __device__ __noinline__ void ray_finish(const DevField& F, const TraceArgs& A, c
   if (O.level) O.level[ray] = lev;
   if (O.status) O.status[ray] = r.status;
 }
+
+mt_status check_trace_params(const mt_trace_params* p, int64_t n_rays);
+void fill_cones(const mt_octree* tree, const mt_trace_params* params, DevCones* C);
+cudaError_t launch_tangent(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O, double* jac,
+                           double* lens, const TraceArgs& A, cudaStream_t stream);
+mt_status run_adjoint(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O,
+                      const double* dL_dxi, double* const* dL_drec, int checkpoint_every, const TraceArgs& A,
+                      cudaStream_t stream);
 
 }  // namespace mt

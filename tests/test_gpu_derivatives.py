@@ -1,0 +1,168 @@
+"""GPU tangent (distortion matrix) and adjoint (gradient with respect to the gridded potential)
+against the FP64 oracle: finite beams of Eqs. (17)-(21), closed forms, and central finite
+differences of the oracle's end points."""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_08744_gb300 import inputs as I
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu(w, precision="fp64", dirs=None, **kw):
+    import torch
+    from paper_2111_08744_gb300 import binding as B
+    d = w.dirs if dirs is None else dirs
+    tree = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, w.levels, w.bg, precision)
+    p = B.TraceParams.from_workload(w, ray_begin=np.array([0, d.shape[1]]) if dirs is not None else None,
+                                    gravity_on=kw.pop("gravity_on", True))
+    res = B.trace_rays_adjoint(tree, p, torch.from_numpy(np.ascontiguousarray(d)).cuda(), **kw)
+    torch.cuda.synchronize()
+    assert tree.device_status() == B.MT_OK
+    tree.free()
+    out = {}
+    for k, v in res.items():
+        out[k] = [t.cpu().numpy() for t in v] if isinstance(v, list) else v.cpu().numpy()
+    return out
+
+
+def quadratic_fn(Q, x0):
+    Q = np.asarray(Q, dtype=np.float64)
+
+    def fn(xc):
+        d = xc - np.asarray(x0, dtype=np.float64)[:, None]
+        rec = np.empty((xc.shape[1], 4))
+        rec[:, 0] = 0.5 * np.einsum("in,ij,jn->n", d, Q, d)
+        rec[:, 1:] = (Q @ d).T
+        return rec
+
+    return fn
+
+
+def test_tangent_is_identity_without_gravity():
+    w = I.config_plain_small()
+    r = _gpu(w, dirs=w.dirs[:, ::17], gravity_on=False)
+    np.testing.assert_allclose(r["jac"][[0, 3]], 1.0, atol=1e-11)
+    np.testing.assert_allclose(r["jac"][[1, 2]], 0.0, atol=1e-11)
+    np.testing.assert_allclose(r["lens"][:4], 0.0, atol=1e-11)
+    np.testing.assert_allclose(r["lens"][4], 1.0, atol=1e-11)
+
+
+def test_tangent_matches_closed_form_for_quadratic_potential():
+    """Same closed form as the oracle pin: A = M - (chi^2/3)(Q_ab - Q_nn delta_ab)."""
+    n, box = 16, 4000.0
+    xo = np.array([2000.0, 2000.0, 2000.0])
+    Q = np.array([[4e-10, 1e-10, 0.0], [1e-10, -2e-10, 0.5e-10], [0.0, 0.5e-10, 1e-10]])
+    lv = [H.coarse_level_from_fn(n, box, quadratic_fn(Q, xo))]
+    dirs = I.healpix_directions(2)
+    w = H.workload(lv, box, n, dirs, z_max=0.45, periodic=0, steps_per_cell=8, observer=xo)
+    r = _gpu(w)
+    A = r["jac"]
+    ref = oracle.bundle_jacobian(w, eps=1e-5)
+    scale = r["chi"].max() ** 2 / 3.0 * np.abs(Q).max()
+    assert np.abs(A - ref).max() < 0.01 * scale
+
+
+@functools.lru_cache(maxsize=None)
+def _plain_beam():
+    w = I.config_plain_small()
+    dirs = np.ascontiguousarray(w.dirs[:, 5::48])
+    return w, dirs
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 3e-5), ("fp32", 3e-4)])
+def test_tangent_matches_oracle_finite_beam(precision, tol):
+    """Eq. (21) with a small beam converges to the tangent of the discrete map."""
+    w, dirs = _plain_beam()
+    r = _gpu(w, precision, dirs=dirs)
+    ref = oracle.bundle_jacobian(w, dirs=dirs, eps=1e-6)
+    dev = np.abs(r["jac"] - ref)
+    # the beam's rays may cross a CIC cell face the central ray does not: allow 2 % outliers
+    frac_bad = np.mean(dev.max(axis=0) > tol)
+    assert frac_bad <= 0.02, (np.sort(dev.max(axis=0))[-5:], frac_bad)
+    assert np.median(dev) < tol / 10
+    assert np.abs(1 - 0.5 * (r["jac"][0] + r["jac"][3])).max() > 1e-4    # lensing is present
+    # Eq. (11) decomposition round trip
+    k, g1, g2, om, det = r["lens"]
+    Rm = np.array([[np.cos(om), -np.sin(om)], [np.sin(om), np.cos(om)]])
+    S = np.array([[1 - k - g1, -g2], [-g2, 1 - k + g1]])
+    A = np.einsum("ijn,jkn->ikn", Rm, S)
+    np.testing.assert_allclose(A.reshape(4, -1), r["jac"], atol=1e-12)
+    np.testing.assert_allclose(det, r["jac"][0] * r["jac"][3] - r["jac"][1] * r["jac"][2], atol=1e-14)
+
+
+def test_tangent_pass_outputs_equal_trace():
+    from tests.gpu_common import compare, run_gpu
+    w, dirs = _plain_beam()
+    r = _gpu(w, dirs=dirs)
+    t = run_gpu(w, "fp64", dirs=dirs)
+    compare({k: r[k] for k in t}, t, 1e-12)
+
+
+# ----------------------------------------------------------------------------- adjoint
+
+@functools.lru_cache(maxsize=None)
+def _adj_workload():
+    w = I.config_amr(n=16, box=200.0, n_levels=1, f1=0.1, ratio=0.3, nside=2, z_max=0.1, seed=41,
+                     name="adj_amr16")
+    return w
+
+
+def _loss_and_xi(w, out):
+    es = oracle.eta_stop(w.bg, float(w.z_max[0]))
+    xi = oracle.xi_on_surface(out, es)
+    ref = w.observer[0][:, None] + w.dirs * (w.bg[-1, 0] - es)
+    return float(((xi - ref) ** 2).sum()), xi - ref
+
+
+def test_adjoint_matches_oracle_finite_differences():
+    """dL/d(record) for L = sum |xi - xi_FLRW|^2 against central differences of the oracle."""
+    import dataclasses
+    import torch
+    w = _adj_workload()
+    base = _gpu(w, jacobian=False, lensing=False)
+    _, dxi = _loss_and_xi(w, base)
+    r = _gpu(w, jacobian=False, lensing=False, dL_dxi=torch.from_numpy(2.0 * dxi).cuda())
+    grads = r["dL_drec"]
+    assert all(np.isfinite(g).all() for g in grads)
+    # the records with the largest gradient components, per level and component type
+    picks = []
+    for lev, g in enumerate(grads):
+        for comp in range(4):
+            flat = np.abs(g[:, :, comp]).ravel()
+            if flat.max() == 0:
+                continue
+            i = int(np.argmax(flat))
+            picks.append((lev, i // g.shape[1], i % g.shape[1], comp))
+    assert len(picks) >= 6
+    errs = []
+    for lev, row, sl, comp in picks:
+        val = w.levels[lev].records[row, sl, comp]
+        g = grads[lev][row, sl, comp]
+        d = 1e-2 * max(abs(val), 1e-7 if comp == 0 else 1e-9)
+        Ls = []
+        for sgn in (+1, -1):
+            lv = [I.Level(l.keys, l.records.copy()) for l in w.levels]
+            lv[lev].records[row, sl, comp] = val + sgn * d
+            o = oracle.trace(dataclasses.replace(w, levels=lv))
+            Ls.append(_loss_and_xi(w, o)[0])
+        fd = (Ls[0] - Ls[1]) / (2 * d)
+        errs.append(abs(fd - g) / max(abs(fd), 1e-30))
+    errs = np.array(errs)
+    assert np.median(errs) < 1e-5, errs
+    assert errs.max() < 1e-3, errs
+
+
+def test_adjoint_checkpoint_interval_does_not_change_gradients():
+    import torch
+    w = _adj_workload()
+    base = _gpu(w, jacobian=False, lensing=False)
+    _, dxi = _loss_and_xi(w, base)
+    g64 = _gpu(w, jacobian=False, lensing=False, dL_dxi=torch.from_numpy(2 * dxi).cuda(), checkpoint_every=64)
+    g7 = _gpu(w, jacobian=False, lensing=False, dL_dxi=torch.from_numpy(2 * dxi).cuda(), checkpoint_every=7)
+    for a, b in zip(g64["dL_drec"], g7["dL_drec"]):
+        np.testing.assert_allclose(a, b, rtol=1e-9, atol=1e-9 * np.abs(a).max())
