@@ -124,7 +124,7 @@ def test_adjoint_matches_oracle_finite_differences():
     import dataclasses
     import torch
     w = _adj_workload()
-    base = _gpu(w, jacobian=False, lensing=False)
+    base = _gpu(w)
     _, dxi = _loss_and_xi(w, base)
     r = _gpu(w, jacobian=False, lensing=False, dL_dxi=torch.from_numpy(2.0 * dxi).cuda())
     grads = r["dL_drec"]
@@ -160,7 +160,7 @@ def test_adjoint_matches_oracle_finite_differences():
 def test_adjoint_checkpoint_interval_does_not_change_gradients():
     import torch
     w = _adj_workload()
-    base = _gpu(w, jacobian=False, lensing=False)
+    base = _gpu(w)
     _, dxi = _loss_and_xi(w, base)
     g64 = _gpu(w, jacobian=False, lensing=False, dL_dxi=torch.from_numpy(2 * dxi).cuda(), checkpoint_every=64)
     g7 = _gpu(w, jacobian=False, lensing=False, dL_dxi=torch.from_numpy(2 * dxi).cuda(), checkpoint_every=7)
