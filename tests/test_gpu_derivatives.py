@@ -139,22 +139,33 @@ def test_adjoint_matches_oracle_finite_differences():
             i = int(np.argmax(flat))
             picks.append((lev, i // g.shape[1], i % g.shape[1], comp))
     assert len(picks) >= 6
-    errs = []
+    errs, kinked = [], []
     for lev, row, sl, comp in picks:
         val = w.levels[lev].records[row, sl, comp]
         g = grads[lev][row, sl, comp]
-        d = 1e-2 * max(abs(val), 1e-7 if comp == 0 else 1e-9)
-        Ls = []
-        for sgn in (+1, -1):
-            lv = [I.Level(l.keys, l.records.copy()) for l in w.levels]
-            lv[lev].records[row, sl, comp] = val + sgn * d
-            o = oracle.trace(dataclasses.replace(w, levels=lv))
-            Ls.append(_loss_and_xi(w, o)[0])
-        fd = (Ls[0] - Ls[1]) / (2 * d)
-        errs.append(abs(fd - g) / max(abs(fd), 1e-30))
+        fds = []
+        for rel in (1e-2, 1e-3):
+            d = rel * max(abs(val), 1e-7 if comp == 0 else 1e-9)
+            Ls, steps = [], []
+            for sgn in (+1, -1):
+                lv = [I.Level(l.keys, l.records.copy()) for l in w.levels]
+                lv[lev].records[row, sl, comp] = val + sgn * d
+                o = oracle.trace(dataclasses.replace(w, levels=lv))
+                Ls.append(_loss_and_xi(w, o)[0])
+                steps.append(o["n_steps"])
+            fds.append(((Ls[0] - Ls[1]) / (2 * d), np.array_equal(steps[0], steps[1])))
+        (fd1, same1), (fd2, same2) = fds
+        # a perturbation that moves a ray across a cell-face or level decision makes L kink:
+        # the two difference quotients then disagree; such picks are reported, not judged
+        if not (same1 and same2) or abs(fd1 - fd2) > 1e-4 * max(abs(fd1), 1e-30):
+            kinked.append((lev, row, sl, comp, fd1, fd2, g))
+            continue
+        errs.append(abs(fd1 - g) / max(abs(fd1), 1e-30))
     errs = np.array(errs)
+    print("relative errors", errs, "kinked", kinked)
+    assert len(errs) >= 6, kinked
     assert np.median(errs) < 1e-5, errs
-    assert errs.max() < 1e-3, errs
+    assert errs.max() < 1e-4, errs
 
 
 def test_adjoint_checkpoint_interval_does_not_change_gradients():
