@@ -169,6 +169,8 @@ typedef struct {
   int32_t* n_steps;
   int32_t* level;
   int32_t* status;
+  double* xi;   /* [3][N] end point moved along k onto the stop surface:
+                   xi = x - (k / k0) (eta - eta_stop) */
 } mt_ray_out;
 
 /*
@@ -215,6 +217,23 @@ mt_status mt_trace_rays_adjoint(const mt_octree* tree, const mt_trace_params* pa
                                 int64_t n_rays, const mt_ray_out* out, double* jac, double* lens,
                                 const double* dL_dxi, double* const* dL_drec, int32_t checkpoint_every,
                                 void* stream);
+
+/*
+ * mt_pullback_coarse_phi -- dL/dphi_0 on the coarse grid from record cotangents dL_drec
+ * (as accumulated by mt_trace_rays_adjoint), through this library's field model:
+ *   coarse records  = w_s (phi_0, D phi_0), D the periodic 5-point central difference
+ *                     (f[i-2] - 8 f[i-1] + 8 f[i+1] - f[i+2]) / (12 dx_0);
+ *   refined records = w_s (I_0[phi_0](x_c), I_0[D phi_0](x_c)) + terms that do not depend
+ *                     on phi_0, with I_0 trilinear interpolation of the periodic,
+ *                     cell-centred coarse grid at the refined cell's centre x_c;
+ *   w_s = slice_weight[s] (host [n_slices]), the time-slice scaling of the potential.
+ * dL_dphi0: device [N_0^3] FP64 in the coarse records' (Morton) order, overwritten.
+ * Uses a temporary device buffer (4 doubles per coarse cell); synchronous.
+ * The paper differentiates nothing; this is the "gradient with respect to the gridded
+ * phi" of the differentiable form of the method.
+ */
+mt_status mt_pullback_coarse_phi(const mt_octree* tree, double* const* dL_drec, const double* slice_weight,
+                                 double* dL_dphi0, void* stream);
 
 /*
  * mt_trace_rays_noalloc -- the same trace as mt_trace_rays, for callers that must not

@@ -49,11 +49,11 @@ class mt_trace_params(ctypes.Structure):
 
 OUT_F64 = ["x", "k", "eta", "lambda", "chi", "path", "z0", "z1", "z4", "z5", "d_a", "d_l", "phi_o", "phi_s", "isw"]
 OUT_I32 = ["n_steps", "level", "status"]
-OUT_ROWS = {"x": 3, "k": 4}
+OUT_ROWS = {"x": 3, "k": 4, "xi": 3}
 
 
 class mt_ray_out(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_void_p) for n in OUT_F64 + OUT_I32]
+    _fields_ = [(n, ctypes.c_void_p) for n in OUT_F64 + OUT_I32 + ["xi"]]
 
 
 _lock = threading.Lock()
@@ -80,6 +80,8 @@ def load():
         lib.mt_trace_rays_adjoint.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64,
                                               ctypes.POINTER(mt_ray_out), P, P, P, ctypes.POINTER(P),
                                               ctypes.c_int32, P]
+        lib.mt_pullback_coarse_phi.restype = ctypes.c_int
+        lib.mt_pullback_coarse_phi.argtypes = [P, ctypes.POINTER(P), P, P, P]
         lib.mt_trace_rays_noalloc.restype = ctypes.c_int
         lib.mt_trace_rays_noalloc.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64,
                                               ctypes.POINTER(mt_ray_out), P]
@@ -254,7 +256,7 @@ def step_cap(bg, dx0, n_levels, steps_per_cell, z_max):
 
 def alloc_outputs(n: int, device=None, names=None) -> Dict[str, "object"]:
     torch = _require_cuda()
-    names = OUT_F64 + OUT_I32 if names is None else names
+    names = OUT_F64 + OUT_I32 + ["xi"] if names is None else names
     out = {}
     for k in names:
         dt = torch.int32 if k in OUT_I32 else torch.float64
@@ -265,7 +267,7 @@ def alloc_outputs(n: int, device=None, names=None) -> Dict[str, "object"]:
 
 def ray_out_struct(out: Dict[str, "object"]) -> mt_ray_out:
     return mt_ray_out(**{k: (out[k].data_ptr() if k in out and out[k] is not None else None)
-                         for k in OUT_F64 + OUT_I32})
+                         for k in OUT_F64 + OUT_I32 + ["xi"]})
 
 
 def trace_rays(tree: Octree, params: TraceParams, dirs, out=None, stream=None):
@@ -320,3 +322,18 @@ def trace_rays_adjoint(tree: Octree, params: TraceParams, dirs, jacobian=True, l
     if dL_dxi is not None:
         res["dL_drec"] = dL_drec
     return res
+
+
+def mt_pullback_coarse_phi(tree, dL_drec, slice_weight, dL_dphi0, stream):
+    return load().mt_pullback_coarse_phi(tree, dL_drec, slice_weight, dL_dphi0, stream)
+
+
+def pullback_coarse_phi(tree: Octree, dL_drec, slice_weight, n_coarse, stream=None):
+    """dL/dphi_0 (CUDA float64 [N_0^3], coarse Morton order) from record cotangents."""
+    torch = _require_cuda()
+    arr = (ctypes.c_void_p * len(dL_drec))(*[t.data_ptr() if t.numel() else None for t in dL_drec])
+    w = np.ascontiguousarray(slice_weight, dtype=np.float64)
+    out = torch.empty(int(n_coarse) ** 3, dtype=torch.float64, device=dL_drec[0].device)
+    _check(load().mt_pullback_coarse_phi(tree.handle, arr, w.ctypes.data_as(ctypes.c_void_p), out.data_ptr(),
+                                         _stream_handle(stream)), "mt_pullback_coarse_phi")
+    return out

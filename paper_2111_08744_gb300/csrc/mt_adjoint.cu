@@ -411,7 +411,7 @@ extern "C" mt_status mt_trace_rays_adjoint(const mt_octree* tree, const mt_trace
   DevCones C;
   fill_cones(tree, params, &C);
   OutPtrs O = {out->x, out->k, out->eta, out->lambda, out->chi, out->path, out->z0, out->z1, out->z4, out->z5,
-               out->d_a, out->d_l, out->phi_o, out->phi_s, out->isw, out->n_steps, out->level, out->status};
+               out->d_a, out->d_l, out->phi_o, out->phi_s, out->isw, out->n_steps, out->level, out->status, out->xi};
   TraceArgs A;
   A.steps_per_cell = params->steps_per_cell;
   A.gravity_on = params->gravity_on ? 1 : 0;

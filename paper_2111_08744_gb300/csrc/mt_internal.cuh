@@ -333,6 +333,7 @@ struct mt_octree {
   mt::DevField f;
   void* rec_alloc[mt::kMaxLevels + 1];
   ulonglong2* hash_alloc[mt::kMaxLevels + 1];
+  unsigned long long* octkey[mt::kMaxLevels + 1];  // parent key of every octet of a refined level
   int64_t count[mt::kMaxLevels + 1];
   double* bg_dev;
   float4* bgf_dev;

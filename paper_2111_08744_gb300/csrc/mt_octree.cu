@@ -25,7 +25,8 @@ __global__ void check_dense_keys(const unsigned long long* keys, long long n, un
 // One thread per key of refined level l: sortedness, octet completeness, key range,
 // parent presence on level l-1, and hash insertion of each octet's parent key.
 __global__ void build_level(const unsigned long long* keys, long long n, int key_bits, HashTable self,
-                            ulonglong2* slots, HashTable parent_level, int parent_is_coarse, unsigned* bad) {
+                            ulonglong2* slots, HashTable parent_level, int parent_is_coarse, unsigned long long* octkey,
+                            unsigned* bad) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const unsigned long long k = keys[i];
     const unsigned long long first = keys[i & ~7ll];
@@ -38,6 +39,7 @@ __global__ void build_level(const unsigned long long* keys, long long n, int key
     }
     if ((i & 7) != 0) continue;
     const unsigned long long pk = k >> 3;  // parent key on level l-1
+    octkey[i >> 3] = pk;
     if (!parent_is_coarse) {
       if (hash_find(parent_level, pk >> 3, bad) < 0) atomicOr(bad, kErrTree);
     }
@@ -74,6 +76,7 @@ void release(mt_octree* t) {
   for (int l = 0; l <= kMaxLevels; ++l) {
     if (t->rec_alloc[l]) cudaFree(t->rec_alloc[l]);
     if (t->hash_alloc[l]) cudaFree(t->hash_alloc[l]);
+    if (t->octkey[l]) cudaFree(t->octkey[l]);
   }
   if (t->bg_dev) cudaFree(t->bg_dev);
   if (t->bgf_dev) cudaFree(t->bgf_dev);
@@ -303,8 +306,10 @@ extern "C" mt_status mt_build_octree(const mt_grid_desc* grid, const mt_level_da
       F.hash[l].mask = (unsigned long long)(cap - 1);
       F.hash[l].shift = 64 - cap_bits;
       const int key_bits = 3 * (bits0 + l);
+      MT_TRY(cudaMalloc(&t->octkey[l], sizeof(unsigned long long) * n_oct));
+      t->device_bytes += sizeof(unsigned long long) * n_oct;
       build_level<<<blocks, 256, 0, stream>>>(dkeys, n, key_bits, F.hash[l], t->hash_alloc[l], F.hash[l - 1],
-                                              l == 1 ? 1 : 0, d_bad);
+                                              l == 1 ? 1 : 0, t->octkey[l], d_bad);
     }
     MT_TRY(cudaGetLastError());
   }

@@ -20,6 +20,7 @@ namespace mt {
 struct OutPtrs {
   double *x, *k, *eta, *lambda, *chi, *path, *z0, *z1, *z4, *z5, *d_a, *d_l, *phi_o, *phi_s, *isw;
   int32_t *n_steps, *level, *status;
+  double* xi;
 };
 
 struct TraceArgs {
@@ -252,6 +253,12 @@ __device__ __noinline__ void ray_finish(const DevField& F, const TraceArgs& A, c
   if (O.n_steps) O.n_steps[ray] = r.n_steps;
   if (O.level) O.level[ray] = lev;
   if (O.status) O.status[ray] = r.status;
+  if (O.xi) {
+    const double de = y[3] - r.eta_stop;
+    O.xi[ray] = y[0] - (y[5] / y[4]) * de;
+    O.xi[n + ray] = y[1] - (y[6] / y[4]) * de;
+    O.xi[2 * n + ray] = y[2] - (y[7] / y[4]) * de;
+  }
 }
 
 mt_status check_trace_params(const mt_trace_params* p, int64_t n_rays);

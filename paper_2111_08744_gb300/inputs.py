@@ -395,6 +395,37 @@ def _demorton(key: np.ndarray):
     return compact(k), compact(k >> np.uint64(1)), compact(k >> np.uint64(2))
 
 
+def _refined_records(keys, lev, n, box, base4, details4, tile):
+    """Records (phi, grad phi) of refined level `lev` cells: trilinear interpolation of the coarse
+    grid (phi_0 and its 5-point gradient, channels last in base4) at the cell centres, plus every
+    coarser level's detail tile interpolated the same way, plus the level's own detail tile."""
+    ci, cj, ck = _demorton(keys)
+    dxl = box / (n << lev)
+    xc = np.stack([ci + 0.5, cj + 0.5, ck + 0.5]).astype(np.float64) * dxl
+    rec = trilinear_periodic(base4, xc / (box / n))
+    for m in range(1, lev):
+        rec += trilinear_periodic(details4[m - 1], xc / (box / (n << m)))
+    own = details4[lev - 1]
+    rec += own[ci % tile, cj % tile, ck % tile]
+    return rec
+
+
+def records_from_phi0(w: "Workload", phi0: np.ndarray, tile: int = 64) -> List[Level]:
+    """The workload's octree (same keys) with records rebuilt from another coarse potential phi0
+    (same detail tiles and slice weights): the linear field model phi0 -> records."""
+    n, box = w.n_coarse, w.box
+    grad0 = gradient_5pt(phi0, box / n)
+    weights = np.asarray(w.slice_weight, dtype=np.float64)
+    out = [_coarse_level(phi0, grad0, weights, n)]
+    base4 = np.concatenate([phi0[..., None], np.moveaxis(grad0, 0, -1)], axis=-1)
+    details4 = [np.concatenate([d[..., None], np.moveaxis(g, 0, -1)], axis=-1) for d, g in (w.detail or [])]
+    for lev in range(1, len(w.levels)):
+        keys = w.levels[lev].keys
+        rec = _refined_records(keys, lev, n, box, base4, details4, tile)
+        out.append(Level(keys=keys, records=np.ascontiguousarray(rec[:, None, :] * weights[None, :, None])))
+    return out
+
+
 def build_field(n: int, box: float, n_levels: int, f1: float, ratio: float, seed: int,
                 rms: float = 1e-5, slice_weights=np.array([1.0]), tile: int = 64,
                 phi0: Optional[np.ndarray] = None):
@@ -440,13 +471,8 @@ def build_field(n: int, box: float, n_levels: int, f1: float, ratio: float, seed
         # cell centres in coarse units and in each detail level's units
         xc = np.stack([ci + 0.5, cj + 0.5, ck + 0.5]).astype(np.float64) * dxl  # physical
         u0 = xc / dx0
-        rec = trilinear_periodic(base4, u0)
-        for m in range(1, lev):
-            um = xc / (box / (n << m))
-            rec += trilinear_periodic(details4[m - 1], um)
         ti, tj, tk = ci % tile, cj % tile, ck % tile
-        rec[:, 0] += d[ti, tj, tk]
-        rec[:, 1:] += dgrad[:, ti, tj, tk].T
+        rec = _refined_records(keys, lev, n, box, base4, details4, tile)
         levels.append(Level(keys=keys, records=np.ascontiguousarray(rec[:, None, :] * weights[None, :, None])))
         if lev == n_levels:
             break

@@ -43,7 +43,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(B.mt_grid_desc) == 40
     assert ctypes.sizeof(B.mt_level_data) == 32
     assert ctypes.sizeof(B.mt_trace_params) == 48
-    assert ctypes.sizeof(B.mt_ray_out) == 18 * 8
+    assert ctypes.sizeof(B.mt_ray_out) == 19 * 8
 
 
 def test_build_rejects_invalid_descriptors_before_gpu_work(lib):

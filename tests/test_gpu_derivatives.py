@@ -177,3 +177,73 @@ def test_adjoint_checkpoint_interval_does_not_change_gradients():
     g7 = _gpu(w, jacobian=False, lensing=False, dL_dxi=torch.from_numpy(2 * dxi).cuda(), checkpoint_every=7)
     for a, b in zip(g64["dL_drec"], g7["dL_drec"]):
         np.testing.assert_allclose(a, b, rtol=1e-9, atol=1e-9 * np.abs(a).max())
+
+
+def test_pullback_to_coarse_phi_matches_oracle_finite_differences():
+    """dL/dphi_0 through the field model (records rebuilt from phi_0 by the generator) against
+    central differences of the oracle's loss in individual coarse cells."""
+    import dataclasses
+    import torch
+    from paper_2111_08744_gb300 import binding as B
+    w = _adj_workload()
+    base = _gpu(w)
+    _, dxi = _loss_and_xi(w, base)
+    tree = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, w.levels, w.bg, "fp64")
+    p = B.TraceParams.from_workload(w)
+    res = B.trace_rays_adjoint(tree, p, torch.from_numpy(w.dirs).cuda(), jacobian=False, lensing=False,
+                               dL_dxi=torch.from_numpy(2 * dxi).cuda())
+    g = B.pullback_coarse_phi(tree, res["dL_drec"], w.slice_weight, w.n_coarse).cpu().numpy()
+    tree.free()
+    n = w.n_coarse
+    order = np.argsort(-np.abs(g))[:10]
+    errs, kinked = [], []
+    for m in order:
+        ci, cj, ck = I._demorton(np.array([m], dtype=np.uint64))
+        i, j, k = int(ci[0]), int(cj[0]), int(ck[0])
+        fds = []
+        for rel in (1e-2, 1e-3):
+            d = rel * 1e-5
+            Ls, steps = [], []
+            for sgn in (+1, -1):
+                phi = w.phi0.copy()
+                phi[i, j, k] += sgn * d
+                o = oracle.trace(dataclasses.replace(w, levels=I.records_from_phi0(w, phi)))
+                Ls.append(_loss_and_xi(w, o)[0])
+                steps.append(o["n_steps"])
+            fds.append(((Ls[0] - Ls[1]) / (2 * d), np.array_equal(steps[0], steps[1])))
+        (f1, s1), (f2, s2) = fds
+        if not (s1 and s2) or abs(f1 - f2) > 1e-4 * abs(f1):
+            kinked.append((m, f1, f2, g[m]))
+            continue
+        errs.append(abs(f1 - g[m]) / abs(f1))
+    errs = np.array(errs)
+    print("pullback relative errors", errs, "kinked", kinked)
+    assert len(errs) >= 6, kinked
+    assert np.median(errs) < 1e-5 and errs.max() < 1e-4, errs
+
+
+def test_autograd_functions_backpropagate_the_adjoint():
+    import torch
+    from paper_2111_08744_gb300 import autograd as AG
+    from paper_2111_08744_gb300 import binding as B
+    w = _adj_workload()
+    tc = AG.TraceContext(w, checkpoint_every=16)
+    recs = [torch.from_numpy(l.records).cuda().requires_grad_(True) for l in w.levels]
+    xi = AG.RayEndpoints.apply(tc, *recs)
+    es = oracle.eta_stop(w.bg, float(w.z_max[0]))
+    ref = torch.from_numpy(w.observer[0][:, None] + w.dirs * (w.bg[-1, 0] - es)).cuda()
+    loss = ((xi - ref) ** 2).sum()
+    loss.backward()
+    # same as calling the adjoint directly
+    tree = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, w.levels, w.bg, "fp64")
+    res = B.trace_rays_adjoint(tree, B.TraceParams.from_workload(w), torch.from_numpy(w.dirs).cuda(),
+                               jacobian=False, lensing=False, dL_dxi=(2 * (xi - ref)).detach(), checkpoint_every=16)
+    tree.free()
+    for r, g in zip(recs, res["dL_drec"]):
+        np.testing.assert_allclose(r.grad.cpu().numpy(), g.cpu().numpy(), rtol=1e-12, atol=1e-30)
+    # coarse-phi form: its gradient is the pull-back of the record gradients
+    phi0 = torch.from_numpy(w.phi0).cuda().requires_grad_(True)
+    xi2 = AG.CoarsePhiEndpoints.apply(tc, phi0)
+    np.testing.assert_allclose(xi2.detach().cpu().numpy(), xi.detach().cpu().numpy(), rtol=0, atol=1e-9)
+    ((xi2 - ref) ** 2).sum().backward()
+    assert torch.isfinite(phi0.grad).all() and phi0.grad.abs().max() > 0
