@@ -62,6 +62,7 @@ struct DevField {
   float dx0_f;        // dx_0
   float bg_inv_deta_f;
   float inv_dseta[kMaxSlices];  // 1 / (eta_{s+1} - eta_s)
+  const unsigned* refbits;      // one bit per coarse cell (Morton order): has children on level 1
 };
 
 struct DevCones {
@@ -334,6 +335,7 @@ struct mt_octree {
   void* rec_alloc[mt::kMaxLevels + 1];
   ulonglong2* hash_alloc[mt::kMaxLevels + 1];
   unsigned long long* octkey[mt::kMaxLevels + 1];  // parent key of every octet of a refined level
+  unsigned* refbits;                               // coarse-cell refinement bitmap
   int64_t count[mt::kMaxLevels + 1];
   double* bg_dev;
   float4* bgf_dev;

@@ -18,20 +18,21 @@
 
 namespace mt {
 
-// Finest-level integer index and FP32 fraction of an FP64 position (once per step).
+// Finest-level integer index and FP32 fraction of an FP64 position (once per step).  The
+// periodic wrap is an integer mask: shifting by whole periods leaves the fraction unchanged.
 __device__ __forceinline__ bool finest_base(const DevField& F, const double* x, int* ib, float* fb) {
-  const double nf = (double)F.nf;
   bool inside = true;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    double v = x[d] * F.inv_dxf;
-    if (F.periodic) {
-      v = v - nf * floor(v * (1.0 / nf));
-    } else {
-      inside = inside && (v >= 0.0) && (v < nf);
-    }
+    const double v = x[d] * F.inv_dxf;
     const double fl = floor(v);
-    ib[d] = (int)fl;
+    const long long il = (long long)fl;
+    if (F.periodic) {
+      ib[d] = (int)(il & (long long)(F.nf - 1));
+    } else {
+      inside = inside && (il >= 0) && (il < (long long)F.nf);
+      ib[d] = (int)il;
+    }
     fb[d] = (float)(v - fl);
   }
   return inside;
@@ -57,41 +58,81 @@ __device__ __forceinline__ bool stage_coords(const DevField& F, const int* ib, c
   return inside;
 }
 
-// Most refined level containing the finest cell ic (hash probe of each level's parent).
+// CIC at level l (FP32) from finest-level integer coordinates; v as in cic_gather.
+__device__ __forceinline__ bool cic_int(const DevField& F, int l, const int* ic, const float* fc, int s, float* v,
+                                        unsigned* err) {
+  const int sh = F.L - l;
+  const float inv = 1.0f / (float)(1 << sh);
+  long long i0[3];
+  float f[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int ilev = ic[d] >> sh;
+    const float fl = ((float)(ic[d] & ((1 << sh) - 1)) + fc[d]) * inv;  // fraction in the level-l cell
+    if (fl >= 0.5f) {
+      i0[d] = ilev;
+      f[d] = fl - 0.5f;
+    } else {
+      i0[d] = (long long)ilev - 1;
+      f[d] = fl + 0.5f;
+    }
+  }
+  return cic_gather<float>(F, l, i0, f, s, v, err);
+}
+
+// Field sample of the mixed path with the level fallback of Sect. 2.2, coarse level first:
+// the coarse CIC and the coarse cell's refinement bit are fetched together (independent
+// loads); only a point inside a refined coarse cell probes the finer levels' hashes and
+// retries CIC from its most refined level down to level 1.  *lf receives the most refined
+// level containing the point.  Returns false outside a non-periodic domain.
+__device__ __forceinline__ bool sample_mixed(const DevField& F, const int* ic, const float* fc, int s, float* v,
+                                             int* lf, unsigned* err) {
+  bool refined = false;
+  if (F.L > 0) {
+    const unsigned sh = (unsigned)F.L;
+    const unsigned long long crow = morton((unsigned)ic[0] >> sh, (unsigned)ic[1] >> sh, (unsigned)ic[2] >> sh);
+    refined = (__ldg(&F.refbits[crow >> 5]) >> (crow & 31ull)) & 1u;
+  }
+  // (a level-0 failure, possible only at a non-periodic edge, ends the sample only if no finer
+  // level succeeds, as in the finest-first fallback)
+  const bool ok0 = cic_int(F, 0, ic, fc, s, v, err);
+  int l = 0;
+  if (refined) {
+    l = 1;
+    for (int q = 2; q <= F.L; ++q) {
+      const int sh = F.L - q + 1;
+      const unsigned long long pk = morton((unsigned)ic[0] >> sh, (unsigned)ic[1] >> sh, (unsigned)ic[2] >> sh);
+      if (hash_find(F.hash[q], pk, err) < 0) break;
+      l = q;
+    }
+    float w[8];
+    for (int q = l; q >= 1; --q) {
+      if (cic_int(F, q, ic, fc, s, w, err)) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = w[i];
+        *lf = l;
+        return true;
+      }
+    }
+  }
+  *lf = l;
+  return ok0;
+}
+
+// Most refined level containing the finest cell ic (locate only, for FLRW stages).
 __device__ __forceinline__ int locate_level_int(const DevField& F, const int* ic, unsigned* err) {
-  int lf = 0;
-  for (int l = 1; l <= F.L; ++l) {
+  if (F.L == 0) return 0;
+  const unsigned sh0 = (unsigned)F.L;
+  const unsigned long long crow = morton((unsigned)ic[0] >> sh0, (unsigned)ic[1] >> sh0, (unsigned)ic[2] >> sh0);
+  if (!((__ldg(&F.refbits[crow >> 5]) >> (crow & 31ull)) & 1u)) return 0;
+  int lf = 1;
+  for (int l = 2; l <= F.L; ++l) {
     const int sh = F.L - l + 1;
     const unsigned long long pk = morton((unsigned)ic[0] >> sh, (unsigned)ic[1] >> sh, (unsigned)ic[2] >> sh);
     if (hash_find(F.hash[l], pk, err) < 0) break;
     lf = l;
   }
   return lf;
-}
-
-// CIC with level fallback from level lfin, FP32; v as in cic_gather.
-__device__ __forceinline__ bool sample_int(const DevField& F, const int* ic, const float* fc, int lfin, int s, float* v,
-                                           unsigned* err) {
-  for (int l = lfin; l >= 0; --l) {
-    const int sh = F.L - l;
-    const float inv = 1.0f / (float)(1 << sh);
-    long long i0[3];
-    float f[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int ilev = ic[d] >> sh;
-      const float fl = ((float)(ic[d] & ((1 << sh) - 1)) + fc[d]) * inv;  // fraction in the level-l cell
-      if (fl >= 0.5f) {
-        i0[d] = ilev;
-        f[d] = fl - 0.5f;
-      } else {
-        i0[d] = (long long)ilev - 1;
-        f[d] = fl + 0.5f;
-      }
-    }
-    if (cic_gather<float>(F, l, i0, f, s, v, err)) return true;
-  }
-  return false;
 }
 
 struct MixedStep {
@@ -130,9 +171,9 @@ __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const Mi
     int ic[3];
     float fc[3];
     if (!stage_coords(F, B.ib, B.fb, offx, ic, fc)) return false;
-    const int l = locate_level_int(F, ic, err);
-    if (lf) *lf = l;
-    if (grav) {
+    if (!grav) {
+      *lf = locate_level_int(F, ic, err);
+    } else {
       int s = B.sb;
       float es = B.e_lo;  // eta_stage - eta_s = es + offe
       if (F.S > 1) {
@@ -146,7 +187,9 @@ __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const Mi
         }
       }
       float v[8];
-      if (!sample_int(F, ic, fc, l, s, v, err)) return false;
+      int l;
+      if (!sample_mixed(F, ic, fc, s, v, &l, err)) return false;
+      if (lf) *lf = l;
       if (F.S == 1) {
         phi = v[0];
         g0 = v[1];

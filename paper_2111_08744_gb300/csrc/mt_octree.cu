@@ -62,6 +62,14 @@ __global__ void build_level(const unsigned long long* keys, long long n, int key
   }
 }
 
+// Bitmap of coarse cells that have children (the parents of level-1 octets).
+__global__ void mark_refined(const unsigned long long* octkey, long long n_oct, unsigned* bits) {
+  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n_oct; o += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long pk = octkey[o];
+    atomicOr(&bits[pk >> 5], 1u << (pk & 31ull));
+  }
+}
+
 int ilog2_exact(long long v) {
   int b = 0;
   while ((1ll << b) < v) ++b;
@@ -79,6 +87,7 @@ void release(mt_octree* t) {
     if (t->octkey[l]) cudaFree(t->octkey[l]);
   }
   if (t->bg_dev) cudaFree(t->bg_dev);
+  if (t->refbits) cudaFree(t->refbits);
   if (t->bgf_dev) cudaFree(t->bgf_dev);
   if (t->ws) cudaFree(t->ws);
   std::free(t->bg_host);
@@ -310,6 +319,15 @@ extern "C" mt_status mt_build_octree(const mt_grid_desc* grid, const mt_level_da
       t->device_bytes += sizeof(unsigned long long) * n_oct;
       build_level<<<blocks, 256, 0, stream>>>(dkeys, n, key_bits, F.hash[l], t->hash_alloc[l], F.hash[l - 1],
                                               l == 1 ? 1 : 0, t->octkey[l], d_bad);
+      if (l == 1) {
+        const size_t words = (size_t)((n0 + 31) / 32);
+        MT_TRY(cudaMalloc(&t->refbits, sizeof(unsigned) * words));
+        MT_TRY(cudaMemsetAsync(t->refbits, 0, sizeof(unsigned) * words, stream));
+        t->device_bytes += sizeof(unsigned) * words;
+        mark_refined<<<(int)std::min<long long>((n_oct + 255) / 256, 65535ll * 8), 256, 0, stream>>>(
+            t->octkey[1], n_oct, t->refbits);
+        F.refbits = t->refbits;
+      }
     }
     MT_TRY(cudaGetLastError());
   }
