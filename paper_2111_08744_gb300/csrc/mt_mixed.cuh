@@ -80,6 +80,24 @@ __device__ __forceinline__ bool cic_int(const DevField& F, int l, const int* ic,
   return cic_gather<float>(F, l, i0, f, s, v, err);
 }
 
+// The refined part of a sample (cold: a minority of stages): probe levels 2..L below a refined
+// coarse cell, then CIC from the most refined level down to level 1.  Returns the level used
+// (0 if every refined level lacks a neighbour) and the most refined level in *lf.
+static __device__ __noinline__ int sample_refined(const DevField& F, const int* ic, const float* fc, int s, float* w,
+                                           int* lf, unsigned* err) {
+  int l = 1;
+  for (int q = 2; q <= F.L; ++q) {
+    const int sh = F.L - q + 1;
+    const unsigned long long pk = morton((unsigned)ic[0] >> sh, (unsigned)ic[1] >> sh, (unsigned)ic[2] >> sh);
+    if (hash_find(F.hash[q], pk, err) < 0) break;
+    l = q;
+  }
+  *lf = l;
+  for (int q = l; q >= 1; --q)
+    if (cic_int(F, q, ic, fc, s, w, err)) return q;
+  return 0;
+}
+
 // Field sample of the mixed path with the level fallback of Sect. 2.2, coarse level first:
 // the coarse CIC and the coarse cell's refinement bit are fetched together (independent
 // loads); only a point inside a refined coarse cell probes the finer levels' hashes and
@@ -96,31 +114,20 @@ __device__ __forceinline__ bool sample_mixed(const DevField& F, const int* ic, c
   // (a level-0 failure, possible only at a non-periodic edge, ends the sample only if no finer
   // level succeeds, as in the finest-first fallback)
   const bool ok0 = cic_int(F, 0, ic, fc, s, v, err);
-  int l = 0;
+  *lf = 0;
   if (refined) {
-    l = 1;
-    for (int q = 2; q <= F.L; ++q) {
-      const int sh = F.L - q + 1;
-      const unsigned long long pk = morton((unsigned)ic[0] >> sh, (unsigned)ic[1] >> sh, (unsigned)ic[2] >> sh);
-      if (hash_find(F.hash[q], pk, err) < 0) break;
-      l = q;
-    }
     float w[8];
-    for (int q = l; q >= 1; --q) {
-      if (cic_int(F, q, ic, fc, s, w, err)) {
+    if (sample_refined(F, ic, fc, s, w, lf, err) > 0) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = w[i];
-        *lf = l;
-        return true;
-      }
+      for (int i = 0; i < 8; ++i) v[i] = w[i];
+      return true;
     }
   }
-  *lf = l;
   return ok0;
 }
 
 // Most refined level containing the finest cell ic (locate only, for FLRW stages).
-__device__ __forceinline__ int locate_level_int(const DevField& F, const int* ic, unsigned* err) {
+static __device__ __noinline__ int locate_level_int(const DevField& F, const int* ic, unsigned* err) {
   if (F.L == 0) return 0;
   const unsigned sh0 = (unsigned)F.L;
   const unsigned long long crow = morton((unsigned)ic[0] >> sh0, (unsigned)ic[1] >> sh0, (unsigned)ic[2] >> sh0);
