@@ -80,54 +80,9 @@ __device__ __forceinline__ bool cic_int(const DevField& F, int l, const int* ic,
   return cic_gather<float>(F, l, i0, f, s, v, err);
 }
 
-// The refined part of a sample (cold: a minority of stages): probe levels 2..L below a refined
-// coarse cell, then CIC from the most refined level down to level 1.  Returns the level used
-// (0 if every refined level lacks a neighbour) and the most refined level in *lf.
-static __device__ __noinline__ int sample_refined(const DevField& F, const int* ic, const float* fc, int s, float* w,
-                                           int* lf, unsigned* err) {
-  int l = 1;
-  for (int q = 2; q <= F.L; ++q) {
-    const int sh = F.L - q + 1;
-    const unsigned long long pk = morton((unsigned)ic[0] >> sh, (unsigned)ic[1] >> sh, (unsigned)ic[2] >> sh);
-    if (hash_find(F.hash[q], pk, err) < 0) break;
-    l = q;
-  }
-  *lf = l;
-  for (int q = l; q >= 1; --q)
-    if (cic_int(F, q, ic, fc, s, w, err)) return q;
-  return 0;
-}
-
-// Field sample of the mixed path with the level fallback of Sect. 2.2, coarse level first:
-// the coarse CIC and the coarse cell's refinement bit are fetched together (independent
-// loads); only a point inside a refined coarse cell probes the finer levels' hashes and
-// retries CIC from its most refined level down to level 1.  *lf receives the most refined
-// level containing the point.  Returns false outside a non-periodic domain.
-__device__ __forceinline__ bool sample_mixed(const DevField& F, const int* ic, const float* fc, int s, float* v,
-                                             int* lf, unsigned* err) {
-  bool refined = false;
-  if (F.L > 0) {
-    const unsigned sh = (unsigned)F.L;
-    const unsigned long long crow = morton((unsigned)ic[0] >> sh, (unsigned)ic[1] >> sh, (unsigned)ic[2] >> sh);
-    refined = (__ldg(&F.refbits[crow >> 5]) >> (crow & 31ull)) & 1u;
-  }
-  // (a level-0 failure, possible only at a non-periodic edge, ends the sample only if no finer
-  // level succeeds, as in the finest-first fallback)
-  const bool ok0 = cic_int(F, 0, ic, fc, s, v, err);
-  *lf = 0;
-  if (refined) {
-    float w[8];
-    if (sample_refined(F, ic, fc, s, w, lf, err) > 0) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = w[i];
-      return true;
-    }
-  }
-  return ok0;
-}
-
-// Most refined level containing the finest cell ic (locate only, for FLRW stages).
-static __device__ __noinline__ int locate_level_int(const DevField& F, const int* ic, unsigned* err) {
+// Most refined level containing the finest cell ic: the coarse refinement bitmap answers
+// level 1 (a 4-byte load from a small, cache-resident array), hash probes the deeper levels.
+__device__ __forceinline__ int locate_level_int(const DevField& F, const int* ic, unsigned* err) {
   if (F.L == 0) return 0;
   const unsigned sh0 = (unsigned)F.L;
   const unsigned long long crow = morton((unsigned)ic[0] >> sh0, (unsigned)ic[1] >> sh0, (unsigned)ic[2] >> sh0);
@@ -178,9 +133,9 @@ __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const Mi
     int ic[3];
     float fc[3];
     if (!stage_coords(F, B.ib, B.fb, offx, ic, fc)) return false;
-    if (!grav) {
-      *lf = locate_level_int(F, ic, err);
-    } else {
+    const int lfin = locate_level_int(F, ic, err);
+    if (lf) *lf = lfin;
+    if (grav) {
       int s = B.sb;
       float es = B.e_lo;  // eta_stage - eta_s = es + offe
       if (F.S > 1) {
@@ -194,9 +149,10 @@ __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const Mi
         }
       }
       float v[8];
-      int l;
-      if (!sample_mixed(F, ic, fc, s, v, &l, err)) return false;
-      if (lf) *lf = l;
+      int l = lfin;
+      for (; l >= 0; --l)
+        if (cic_int(F, l, ic, fc, s, v, err)) break;
+      if (l < 0) return false;
       if (F.S == 1) {
         phi = v[0];
         g0 = v[1];
