@@ -269,6 +269,97 @@ def run_ours(args, ws, rank):
     tree.free()
 
 
+def run_batched(args, ws, rank):
+    """Batched light cones: 64 observers in the benchmark field, z_max ~ U[0.3, 2], ray counts
+    log-uniform in [1e4, 1e6] (NESTED HEALPix sub-patches); one persistent launch replayed from
+    a CUDA graph after the launch-shape autotuner; compared with one launch per cone and with
+    the FP64-field form on a ray sample."""
+    import torch
+
+    from paper_2111_08744_gb300 import autotune as AT
+    from paper_2111_08744_gb300 import binding as B
+    from paper_2111_08744_gb300 import build as Bd
+    from paper_2111_08744_gb300 import inputs as I
+
+    Bd.build()
+    base = I.cached(I.config_amr)
+    w = I.batched_cones(base, n_cones=64, seed=4113, scale=args.batched_scale)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tree = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, I.fp32_levels(w), w.bg, "fp32")
+    params = B.TraceParams.from_workload(w)
+    dirs = torch.from_numpy(w.dirs).to(dev)
+    tune = AT.autotune(tree, params, dirs, sample=262144, repeats=1)
+    g = AT.TraceGraph(tree, params, dirs)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(max(0, args.warmup - 1)):
+        g.replay()
+    torch.cuda.synchronize()
+    steps = int(g.out["n_steps"].sum().item())
+    ts = []
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ck = clocks.stop()
+    ms = float(np.mean(ts))
+    # one launch per cone (same kernel, same launch shape)
+    outs = B.alloc_outputs(w.n_rays, dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for c in range(w.observer.shape[0]):
+        lo, hi = int(w.ray_begin[c]), int(w.ray_begin[c + 1])
+        if hi == lo:
+            continue
+        p1 = B.TraceParams(w.observer[c:c + 1], w.z_max[c:c + 1], [0, hi - lo], w.steps_per_cell,
+                           max_steps=params.c.max_steps)
+        B.trace_rays(tree, p1, dirs[:, lo:hi].contiguous(), {k: v[..., lo:hi] for k, v in outs.items()})
+    b.record()
+    torch.cuda.synchronize()
+    ms_unbatched = a.elapsed_time(b)
+    # FP64-field form on a seeded 1/16 sample of the rays (accuracy reference and speed)
+    rng = np.random.Generator(np.random.PCG64(5))
+    idx = np.sort(rng.choice(w.n_rays, size=w.n_rays // 16, replace=False))
+    cone = np.searchsorted(w.ray_begin, idx, side="right") - 1
+    counts = np.bincount(cone, minlength=w.observer.shape[0])
+    ps = B.TraceParams(w.observer, w.z_max, np.concatenate([[0], np.cumsum(counts)]), w.steps_per_cell,
+                       max_steps=params.c.max_steps)
+    t64 = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, w.levels, w.bg, "fp64")
+    d_s = dirs[:, torch.from_numpy(idx).to(dev)].contiguous()
+    a.record()
+    o64 = B.trace_rays(t64, ps, d_s)
+    b.record()
+    torch.cuda.synchronize()
+    ms64 = a.elapsed_time(b)
+    o32 = {k: v[..., torch.from_numpy(idx).to(dev)] for k, v in g.out.items()}
+    err = {}
+    for k, fl in (("x", 1.0), ("z5", 1e-6), ("chi", 1.0), ("d_l", 1.0)):
+        r = o64[k].double()
+        err[k] = float(((o32[k].double() - r).abs() / r.abs().clamp_min(fl)).max().item())
+    steps64 = int(o64["n_steps"].sum().item())
+    line = {"metric": "rays/s, batched light cones (64 observers, z_max 0.3-2) in one persistent launch",
+            "value": w.n_rays / (ms * 1e-3), "unit": "rays/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 state / f32 field", "data": "synthetic",
+            "config": {"workload": "64 light cones in the AMR 256^3 + 3 levels field", "n_rays": w.n_rays,
+                       "n_cones": int(w.observer.shape[0]), "rk4_steps": steps, "launch": tune["best"],
+                       "graph": True},
+            "steps_per_s": steps / (ms * 1e-3), "autotune_ms": tune["ms"],
+            "unbatched_ms": ms_unbatched, "unbatched_rays_per_s": w.n_rays / (ms_unbatched * 1e-3),
+            "fp64_field_sample": {"rays": int(idx.size), "ms": ms64, "steps_per_s": steps64 / (ms64 * 1e-3),
+                                  "max_rel_err_fp32_vs_fp64": err},
+            "clocks": ck, "gpu_launches": args.steps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    t64.free()
+    tree.free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -278,10 +369,15 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rays", type=int, default=0, help="trace a seeded subset of N rays (profiling only)")
+    ap.add_argument("--workload", default="amr", choices=["amr", "batched"],
+                    help="amr: the headline benchmark; batched: 64 light cones (separate report)")
+    ap.add_argument("--batched-scale", type=float, default=1.0)
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "batched":
+        run_batched(args, ws, rank)
     else:
         run_ours(args, ws, rank)
     if ws > 1:

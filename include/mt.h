@@ -268,6 +268,14 @@ mt_status mt_trace_rays_noalloc(const mt_octree* tree, const mt_trace_params* pa
                                 int64_t n_rays, const mt_ray_out* out, void* stream);
 
 /*
+ * mt_set_launch_config -- launch shape of mt_trace_rays on this octree (tuning only; results
+ * do not depend on it): block_size 64, 128 or 256 threads (0: default 128), blocks_per_sm
+ * >= 1 to cap the persistent grid at num_SMs x blocks_per_sm (0: as many as fit).
+ * Errors: MT_ERR_INVALID_ARG.
+ */
+mt_status mt_set_launch_config(mt_octree* tree, int32_t block_size, int32_t blocks_per_sm);
+
+/*
  * mt_device_status -- synchronise `stream` and return the device-side flag of
  * the last kernels on this octree (MT_OK, MT_ERR_OOB, MT_ERR_TIMEOUT), then
  * clear it.

@@ -85,6 +85,8 @@ def load():
         lib.mt_trace_rays_noalloc.restype = ctypes.c_int
         lib.mt_trace_rays_noalloc.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64,
                                               ctypes.POINTER(mt_ray_out), P]
+        lib.mt_set_launch_config.restype = ctypes.c_int
+        lib.mt_set_launch_config.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
         lib.mt_device_status.restype = ctypes.c_int
         lib.mt_device_status.argtypes = [P, P]
         lib.mt_free.restype = None
@@ -140,6 +142,10 @@ def mt_trace_rays_adjoint(tree, params, dirs, n_rays, out, jac, lens, dL_dxi, dL
 
 def mt_trace_rays_noalloc(tree, params, dirs, n_rays, out, stream):
     return load().mt_trace_rays_noalloc(tree, params, dirs, n_rays, out, stream)
+
+
+def mt_set_launch_config(tree, block_size, blocks_per_sm):
+    return load().mt_set_launch_config(tree, block_size, blocks_per_sm)
 
 
 def mt_device_status(tree, stream):
@@ -209,6 +215,9 @@ class Octree:
         nbytes = ctypes.c_int64()
         _check(load().mt_octree_info(self.handle, cells, ctypes.byref(nbytes)), "mt_octree_info")
         return list(cells), int(nbytes.value)
+
+    def set_launch_config(self, block_size=0, blocks_per_sm=0):
+        _check(load().mt_set_launch_config(self.handle, int(block_size), int(blocks_per_sm)), "mt_set_launch_config")
 
     def device_status(self, stream=None) -> int:
         return load().mt_device_status(self.handle, _stream_handle(stream))

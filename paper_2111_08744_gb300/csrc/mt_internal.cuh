@@ -344,6 +344,8 @@ struct mt_octree {
   unsigned long long* ws;  // [0] ray queue counter, [1] error flags
   int64_t device_bytes;
   int num_sms;
+  int launch_block;  // trace kernel threads per block (0: default 128)
+  int launch_bps;    // trace kernel blocks per SM (0: as many as fit)
 };
 
 namespace mt {

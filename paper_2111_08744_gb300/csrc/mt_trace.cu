@@ -24,9 +24,10 @@ __device__ void ray_init(const DevField& F, const DevCones& C, const double* __r
   r = ray_start<T>(F, C.obs[c], C.eta_stop[c], dirs, n, ray, grav, err);
 }
 
-template <class T>
-__global__ void __launch_bounds__(kBlock, 4) trace_kernel(DevField F, DevCones C, const double* __restrict__ dirs,
-                                                       OutPtrs O, TraceArgs A, unsigned long long* ws) {
+// BS threads per block; the register budget (128 per thread) is the same for every block size.
+template <class T, int BS>
+__global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCones C, const double* __restrict__ dirs,
+                                                              OutPtrs O, TraceArgs A, unsigned long long* ws) {
   unsigned* err = (unsigned*)(ws + 1);
   const unsigned lane = threadIdx.x & 31u;
   const long long n = A.n_rays;
@@ -63,15 +64,35 @@ __global__ void __launch_bounds__(kBlock, 4) trace_kernel(DevField F, DevCones C
   }
 }
 
-template <class T>
+template <class T, int BS>
 int blocks_per_sm() {
   static int cached = -1;
   if (cached < 0) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<T>, kBlock, 0) != cudaSuccess || b < 1) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<T, BS>, BS, 0) != cudaSuccess || b < 1) b = 1;
     cached = b;
   }
   return cached;
+}
+
+template <class T, int BS>
+void launch_trace_bs(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O,
+                     const TraceArgs& A, cudaStream_t stream) {
+  int bps = blocks_per_sm<T, BS>();
+  if (tree->launch_bps > 0 && tree->launch_bps < bps) bps = tree->launch_bps;
+  trace_kernel<T, BS><<<tree->num_sms * bps, BS, 0, stream>>>(tree->f, C, dirs, O, A, tree->ws);
+}
+
+// Launch shape: the octree's configuration (mt_set_launch_config), default 128 threads and as
+// many blocks per SM as fit.
+template <class T>
+void launch_trace(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O, const TraceArgs& A,
+                  cudaStream_t stream) {
+  switch (tree->launch_block) {
+    case 64: launch_trace_bs<T, 64>(tree, C, dirs, O, A, stream); break;
+    case 256: launch_trace_bs<T, 256>(tree, C, dirs, O, A, stream); break;
+    default: launch_trace_bs<T, 128>(tree, C, dirs, O, A, stream); break;
+  }
 }
 
 }  // namespace mt
@@ -130,14 +151,21 @@ extern "C" mt_status mt_trace_rays(const mt_octree* tree, const mt_trace_params*
   cudaError_t e = cudaMemsetAsync(tree->ws, 0, sizeof(unsigned long long), stream);
   if (e == cudaSuccess) {
     if (tree->precision == MT_FIELD_FP64) {
-      int grid = tree->num_sms * blocks_per_sm<double>();
-      trace_kernel<double><<<grid, kBlock, 0, stream>>>(tree->f, C, dirs, O, A, tree->ws);
+      launch_trace<double>(tree, C, dirs, O, A, stream);
     } else {
-      int grid = tree->num_sms * blocks_per_sm<float>();
-      trace_kernel<float><<<grid, kBlock, 0, stream>>>(tree->f, C, dirs, O, A, tree->ws);
+      launch_trace<float>(tree, C, dirs, O, A, stream);
     }
     e = cudaGetLastError();
   }
   if (prev >= 0 && prev != tree->device) cudaSetDevice(prev);
   return e == cudaSuccess ? MT_OK : MT_ERR_CUDA;
+}
+
+extern "C" mt_status mt_set_launch_config(mt_octree* tree, int32_t block_size, int32_t blocks_per_sm) {
+  if (!tree) return MT_ERR_INVALID_ARG;
+  if (block_size != 0 && block_size != 64 && block_size != 128 && block_size != 256) return MT_ERR_INVALID_ARG;
+  if (blocks_per_sm < 0) return MT_ERR_INVALID_ARG;
+  tree->launch_block = block_size;
+  tree->launch_bps = blocks_per_sm;
+  return MT_OK;
 }
