@@ -127,6 +127,17 @@ def max_over_ranks(v, ws):
     return float(t.item())
 
 
+def rank_workload(w, rank, ws):
+    """Weak scaling: each rank traces its own light cone (same field, same rays) from an
+    observer shifted by rank/ws of the box along x; no data moves between ranks."""
+    if ws == 1:
+        return w
+    import dataclasses
+    obs = w.observer.copy()
+    obs[:, 0] = (obs[:, 0] + w.box * rank / ws) % w.box
+    return dataclasses.replace(w, observer=obs)
+
+
 def oracle_sample(w, budget_s=15.0):
     """Time the CPU oracle on a bounded, seeded sample of the rays; returns (rays/s, n, threads, secs)."""
     import oracle
@@ -174,7 +185,7 @@ def run_ours(args, ws, rank):
     from paper_2111_08744_gb300 import inputs as I
 
     Bd.build()
-    w = I.cached(I.config_amr)
+    w = rank_workload(I.cached(I.config_amr), rank, ws)
     if args.rays:
         # a seeded subset of the rays (profiling captures of a short launch; not a bench line)
         rng = np.random.Generator(np.random.PCG64(7))
