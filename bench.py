@@ -371,6 +371,75 @@ def run_batched(args, ws, rank):
     tree.free()
 
 
+def run_large(args, ws, rank):
+    """The largest configuration: 1024^3 coarse grid in 2.6 h^-1 Gpc + 4 levels (3 % of the
+    volume, 1/8 per level), four time slices (z = 2, 1, 0.5, 0), FP32 records (~135 GB, built on
+    the GPU and borrowed by the octree), 50,331,648 HEALPix rays (nside 2048) to z = 2."""
+    import torch
+
+    from paper_2111_08744_gb300 import binding as B
+    from paper_2111_08744_gb300 import build as Bd
+    from paper_2111_08744_gb300 import inputs as I
+
+    Bd.build()
+    t0 = time.perf_counter()
+    kw = {}
+    if args.large_n:
+        kw = {"n": args.large_n, "box": 2600.0 * args.large_n / 1024, "nside": args.large_nside}
+    w = I.config_large_gpu(**kw)
+    t_gen = time.perf_counter() - t0
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.perf_counter()
+    tree = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, w.levels, w.bg, "fp32", residency=B.MT_DEVICE_BORROW)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    cells, nbytes = tree.info()
+    params = B.TraceParams.from_workload(w)
+    dirs = torch.from_numpy(w.dirs).to(dev)
+    n = w.n_rays
+    out = B.alloc_outputs(n, dev)
+    for _ in range(args.warmup):
+        B.trace_rays(tree, params, dirs, out)
+    torch.cuda.synchronize()
+    ts = []
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for i in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        B.trace_rays(tree, params, dirs, out)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ck = clocks.stop()
+    st = tree.device_status()
+    steps = int(out["n_steps"].sum().item())
+    status = torch.bincount(out["status"].long(), minlength=4).tolist()
+    levels = torch.bincount(out["level"].long() + 1, minlength=6).tolist()
+    ms = float(np.mean(ts))
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = FIELD_BYTES_PER_STEP * steps / (ms * 1e-3) / 1e9
+    line = {"metric": "rays/s to z=2, largest AMR configuration", "value": n / (ms * 1e-3), "unit": "rays/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 state / f32 field", "data": "synthetic",
+            "config": {"workload": w.name, "n_rays": n, "cells_per_level": cells, "device_bytes_octree": nbytes,
+                       "n_slices": w.n_slices, "z_max": float(w.z_max[0])},
+            "steps_per_s": steps / (ms * 1e-3), "rk4_steps_per_step": steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "kernel": "trace_kernel<float>"},
+            "generation_s": t_gen, "build_s": t_build, "device_status": st, "ray_status_counts": status,
+            "end_level_counts": levels[1:], "clocks": ck, "step_ms_all": ts, "gpu_launches": args.steps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tree.free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -380,15 +449,19 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rays", type=int, default=0, help="trace a seeded subset of N rays (profiling only)")
-    ap.add_argument("--workload", default="amr", choices=["amr", "batched"],
+    ap.add_argument("--workload", default="amr", choices=["amr", "batched", "large"],
                     help="amr: the headline benchmark; batched: 64 light cones (separate report)")
     ap.add_argument("--batched-scale", type=float, default=1.0)
+    ap.add_argument("--large-n", type=int, default=0, help="coarse size of a reduced large run (0: 1024)")
+    ap.add_argument("--large-nside", type=int, default=2048)
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, ws, rank)
     elif args.workload == "batched":
         run_batched(args, ws, rank)
+    elif args.workload == "large":
+        run_large(args, ws, rank)
     else:
         run_ours(args, ws, rank)
     if ws > 1:

@@ -183,10 +183,13 @@ class Octree:
             keys, rec = lv.keys, lv.records
             if isinstance(rec, torch.Tensor):
                 rec = rec.to(tdt).contiguous()
-                k = keys.contiguous() if isinstance(keys, torch.Tensor) else \
-                    torch.from_numpy(np.ascontiguousarray(keys, dtype=np.uint64).view(np.int64)).cuda()
-                self._keep += [rec, k]
-                arr[i] = mt_level_data(k.data_ptr(), rec.data_ptr(), int(k.numel()),
+                if keys is None:  # dense coarse level: keys implied
+                    k = None
+                else:
+                    k = keys.contiguous() if isinstance(keys, torch.Tensor) else \
+                        torch.from_numpy(np.ascontiguousarray(keys, dtype=np.uint64).view(np.int64)).cuda()
+                self._keep += [rec] + ([k] if k is not None else [])
+                arr[i] = mt_level_data(k.data_ptr() if k is not None else None, rec.data_ptr(), int(rec.shape[0]),
                                        MT_DEVICE_COPY if residency is None else residency, 0)
             else:
                 k = np.ascontiguousarray(keys, dtype=np.uint64)

@@ -585,3 +585,202 @@ def cached(builder, cache_dir: Optional[str] = None, **kwargs) -> Workload:
 def fp32_levels(w: Workload) -> List[Level]:
     """The same records rounded to float32 (the mixed-precision field)."""
     return [Level(keys=l.keys, records=l.records.astype(np.float32)) for l in w.levels]
+
+
+# --------------------------------------------------------------------------
+# Large workloads generated on the GPU (same field model, torch CUDA tensors)
+# --------------------------------------------------------------------------
+
+def _t_morton(i, j, k):
+    """Morton keys of int64 CUDA tensors (same bit layout as morton3)."""
+    import torch
+
+    def spread(v):
+        v = v & 0x1FFFFF
+        v = (v | (v << 32)) & 0x1F00000000FFFF
+        v = (v | (v << 16)) & 0x1F0000FF0000FF
+        v = (v | (v << 8)) & 0x100F00F00F00F00F
+        v = (v | (v << 4)) & 0x10C30C30C30C30C3
+        v = (v | (v << 2)) & 0x1249249249249249
+        return v
+
+    return spread(i) | (spread(j) << 1) | (spread(k) << 2)
+
+
+def _t_demorton(key):
+    def compact(v):
+        v = v & 0x1249249249249249
+        v = (v | (v >> 2)) & 0x10C30C30C30C30C3
+        v = (v | (v >> 4)) & 0x100F00F00F00F00F
+        v = (v | (v >> 8)) & 0x1F0000FF0000FF
+        v = (v | (v >> 16)) & 0x1F00000000FFFF
+        v = (v | (v >> 32)) & 0x1FFFFF
+        return v
+
+    return compact(key), compact(key >> 1), compact(key >> 2)
+
+
+def _t_trilinear(grid, xc_units):
+    """Trilinear interpolation of a periodic cell-centred [n, n, n] CUDA grid at points [3, M]
+    given in cell units (FP32 weights); chunked to bound temporaries."""
+    import torch
+    n = grid.shape[0]
+    flat = grid.reshape(-1)
+    out = torch.empty(xc_units.shape[1], dtype=grid.dtype, device=grid.device)
+    step = 1 << 25
+    for a in range(0, xc_units.shape[1], step):
+        u = xc_units[:, a:a + step] - 0.5
+        i0 = torch.floor(u)
+        f = (u - i0).to(grid.dtype)
+        i0 = i0.to(torch.int64)
+        acc = torch.zeros(u.shape[1], dtype=grid.dtype, device=grid.device)
+        for cx in (0, 1):
+            wx = f[0] if cx else 1 - f[0]
+            ix = ((i0[0] + cx) % n) * (n * n)
+            for cy in (0, 1):
+                wy = wx * (f[1] if cy else 1 - f[1])
+                iy = ix + ((i0[1] + cy) % n) * n
+                for cz in (0, 1):
+                    w = wy * (f[2] if cz else 1 - f[2])
+                    acc += w * flat[iy + ((i0[2] + cz) % n)]
+        out[a:a + step] = acc
+    return out
+
+
+def _t_threshold(values, frac, seed, sample=1 << 23):
+    """Value above which about `frac` of `values` lie (quantile of a seeded subsample)."""
+    import torch
+    g = torch.Generator(device=values.device)
+    g.manual_seed(seed)
+    idx = torch.randint(0, values.numel(), (min(sample, values.numel()),), generator=g, device=values.device)
+    return torch.quantile(values.reshape(-1)[idx].float(), 1.0 - frac).item()
+
+
+@dataclasses.dataclass
+class GpuLevel:
+    keys: "object"      # int64 CUDA tensor (Morton keys), None for the dense coarse level
+    records: "object"   # float32 CUDA tensor [count, n_slices, 4]
+
+
+def config_large_gpu(n: int = 1024, box: float = 2600.0, n_levels: int = 4, f1: float = 0.03, ratio: float = 0.125,
+                     nside: int = 2048, z_max: float = 2.0, seed: int = 2115, steps_per_cell: int = 4,
+                     slice_z=(2.0, 1.0, 0.5, 0.0), rms: float = 1e-5, tile: int = 64, device: str = "cuda",
+                     ray_subset: Optional[np.ndarray] = None):
+    """The large AMR workload built on the GPU: n^3 coarse grid plus n_levels refined levels
+    (volume fraction f1, then x ratio per level), len(slice_z) time slices, HEALPix NESTED rays.
+    Same field model as build_field (records in FP32): coarse GRF phi_0 from PCG64 white noise,
+    5-point gradient, refined records = trilinear interpolation of the coarse grid at the cell
+    centre + coarser detail tiles + the level's own detail tile, slice s scaled by g(a_s)."""
+    import torch
+    dev = torch.device(device)
+    om = 0.31
+    bg = background_table(om)
+    a_s = 1.0 / (1.0 + np.asarray(slice_z, dtype=np.float64))
+    order = np.argsort(a_s)
+    a_s = a_s[order]
+    eta_s = eta_of_a(a_s, om)
+    if a_s[-1] == 1.0:
+        eta_s[-1] = bg[-1, 0]
+    gw = growth_over_a(a_s, om)
+    wt = torch.tensor(gw, dtype=torch.float32, device=dev)
+    dx0 = box / n
+    # coarse GRF: PCG64 white noise -> FFT -> sqrt(P(k)), P ~ k^-3 -> rms
+    rng = np.random.Generator(np.random.PCG64(seed))
+    phi = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    for i in range(n):
+        phi[i] = torch.from_numpy(rng.standard_normal((n, n), dtype=np.float32)).to(dev)
+    kf = 2.0 * math.pi / box
+    k1 = torch.fft.fftfreq(n, d=1.0 / n, device=dev) * kf
+    kz = torch.fft.rfftfreq(n, d=1.0 / n, device=dev) * kf
+    fk = torch.fft.rfftn(phi)
+    del phi
+    for i in range(n):  # in place, plane by plane: amplitude k^-1.5, k = 0 removed
+        kk = torch.sqrt(k1[i] ** 2 + k1[:, None] ** 2 + kz[None, :] ** 2)
+        amp = torch.where(kk > 0, kk.clamp_min(1e-30) ** -1.5, torch.zeros_like(kk))
+        fk[i] *= amp
+    phi0 = torch.fft.irfftn(fk, s=(n, n, n))
+    # density estimate for refinement: +laplacian (spectral), unit variance
+    for i in range(n):
+        fk[i] *= -(k1[i] ** 2 + k1[:, None] ** 2 + kz[None, :] ** 2)
+    delta = torch.fft.irfftn(fk, s=(n, n, n))
+    del fk
+    phi0 -= phi0.mean()
+    phi0 *= rms / torch.sqrt((phi0.double() ** 2).mean()).float()
+    delta /= torch.sqrt((delta.double() ** 2).mean()).float()
+    grad0 = [(torch.roll(phi0, 2, ax) - 8.0 * torch.roll(phi0, 1, ax) + 8.0 * torch.roll(phi0, -1, ax)
+              - torch.roll(phi0, -2, ax)) / (12.0 * dx0) for ax in range(3)]
+    # level 0: records in Morton order, [count, S, 4]
+    S = len(a_s)
+    n0 = n ** 3
+    rec0 = torch.empty((n0, S, 4), dtype=torch.float32, device=dev)
+    ar = torch.arange(n, device=dev, dtype=torch.int64)
+    for i in range(n):
+        jj, kk = torch.meshgrid(ar, ar, indexing="ij")
+        keys = _t_morton(torch.full_like(jj, i), jj, kk).reshape(-1)
+        vals = torch.empty((n * n, 4), dtype=torch.float32, device=dev)
+        vals[:, 0] = phi0[i].reshape(-1)
+        for ax in range(3):
+            vals[:, 1 + ax] = grad0[ax][i].reshape(-1)
+        rec0[keys] = vals[:, None, :] * wt[None, :, None]
+    levels = [GpuLevel(keys=None, records=rec0)]
+    # refined levels
+    thr = _t_threshold(delta, f1, seed)
+    sel = torch.nonzero(delta.reshape(-1) > thr).squeeze(1)
+    ci, cj, ck = sel // (n * n), (sel // n) % n, sel % n
+    parents = torch.sort(_t_morton(ci, cj, ck)).values
+    del sel, ci, cj, ck
+    n_oct = max(1, int(round(math.log2(n / 2))))
+    detail_rms = rms / math.sqrt(n_oct)
+    details = []
+    for lev in range(1, n_levels + 1):
+        dxl = box / (n << lev)
+        keys = ((parents[:, None] << 3) | torch.arange(8, device=dev)[None, :]).reshape(-1)
+        d = gaussian_potential(tile, tile * dxl, seed * 131 + lev, detail_rms,
+                               band=(0.5 * math.pi / dxl, math.pi / dxl * 1.0001))
+        dgrad = gradient_5pt(d, dxl)
+        dt = torch.from_numpy(d.astype(np.float32)).to(dev)
+        dgt = torch.from_numpy(dgrad.astype(np.float32)).to(dev)
+        details.append((dt, dgt))
+        cnt = keys.numel()
+        rec = torch.empty((cnt, S, 4), dtype=torch.float32, device=dev)
+        step = 1 << 26
+        dens_all = torch.empty(cnt, dtype=torch.float32, device=dev) if lev < n_levels else None
+        if dens_all is not None:
+            lap = torch.from_numpy(spectral_laplacian(d, tile * dxl).astype(np.float32)).to(dev)
+            lap /= torch.sqrt((lap.double() ** 2).mean()).float()
+        for a in range(0, cnt, step):
+            kc = keys[a:a + step]
+            ci, cj, ck = _t_demorton(kc)
+            xc = (torch.stack([ci, cj, ck]).double() + 0.5) * dxl
+            vals = torch.empty((kc.numel(), 4), dtype=torch.float32, device=dev)
+            u0 = xc / dx0
+            vals[:, 0] = _t_trilinear(phi0, u0)
+            for ax in range(3):
+                vals[:, 1 + ax] = _t_trilinear(grad0[ax], u0)
+            for m in range(1, lev):
+                dm, dgm = details[m - 1]
+                um = xc / (box / (n << m))
+                vals[:, 0] += _t_trilinear(dm, um)
+                for ax in range(3):
+                    vals[:, 1 + ax] += _t_trilinear(dgm[ax], um)
+            ti, tj, tk = ci % tile, cj % tile, ck % tile
+            vals[:, 0] += dt[ti, tj, tk]
+            for ax in range(3):
+                vals[:, 1 + ax] += dgt[ax][ti, tj, tk]
+            rec[a:a + step] = vals[:, None, :] * wt[None, :, None]
+            if dens_all is not None:
+                dens_all[a:a + step] = _t_trilinear(delta, u0) + 0.5 * lap[ti, tj, tk]
+        levels.append(GpuLevel(keys=keys, records=rec))
+        if lev == n_levels:
+            break
+        thr = _t_threshold(dens_all, ratio, seed + lev)
+        parents = torch.sort(keys[dens_all > thr]).values
+        del dens_all
+    del delta, grad0
+    dirs = healpix_directions(nside, nest=True, ipix=ray_subset)
+    w = Workload(name=f"large_{n}cube_L{n_levels}_nside{nside}_z{z_max:g}", box=box, n_coarse=n, periodic=1,
+                 slice_eta=eta_s, slice_weight=gw, levels=levels, bg=bg, omega_m=om,
+                 observer=np.array([[0.5 * box] * 3]), z_max=np.array([z_max]),
+                 ray_begin=np.array([0, dirs.shape[1]], dtype=np.int64), dirs=dirs, steps_per_cell=steps_per_cell,
+                 phi0=None, detail=None)
+    return w
