@@ -440,6 +440,59 @@ def run_large(args, ws, rank):
     tree.free()
 
 
+def run_diff(args, ws, rank):
+    """Differentiation: 1024 x 1024 rays over 10 x 10 deg to z = 1 through the 128^3 + 3 levels
+    field (FP64 records); timings of the forward trace, the forward-mode distortion matrix and the
+    reverse-mode gradient of L = sum |xi - xi_FLRW|^2 with respect to the records and to phi_0."""
+    import torch
+
+    from paper_2111_08744_gb300 import binding as B
+    from paper_2111_08744_gb300 import build as Bd
+    from paper_2111_08744_gb300 import inputs as I
+
+    Bd.build()
+    w = I.cached(I.config_diff, n_pix=args.diff_pix)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tree = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, w.levels, w.bg, "fp64")
+    params = B.TraceParams.from_workload(w)
+    dirs = torch.from_numpy(w.dirs).to(dev)
+    n = w.n_rays
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        r = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return r, a.elapsed_time(b)
+
+    out, _ = timed(lambda: B.trace_rays(tree, params, dirs))
+    out, ms_fwd = timed(lambda: B.trace_rays(tree, params, dirs))
+    steps = int(out["n_steps"].sum().item())
+    tan, ms_tan = timed(lambda: B.trace_rays_adjoint(tree, params, dirs, jacobian=True, lensing=True))
+    # reference end points: the same rays traced without gravity (FLRW)
+    ref = B.trace_rays(tree, B.TraceParams.from_workload(w, gravity_on=False), dirs)["xi"]
+    dxi = 2.0 * (tan["xi"] - ref)
+    adj, ms_adj = timed(lambda: B.trace_rays_adjoint(tree, params, dirs, jacobian=False, lensing=False,
+                                                     dL_dxi=dxi, checkpoint_every=64))
+    g0, ms_pb = timed(lambda: B.pullback_coarse_phi(tree, adj["dL_drec"], w.slice_weight, w.n_coarse))
+    lens = tan["lens"]
+    line = {"metric": "differentiable ray tracing: forward, distortion matrix and gradient time",
+            "value": n / (ms_tan * 1e-3), "unit": "rays/s (distortion matrix)", "n_gpus": ws,
+            "steps": 1, "warmup": 1, "ms_per_step": ms_tan, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n_rays": n, "rk4_steps": steps, "checkpoint_every": 64},
+            "forward_ms": ms_fwd, "tangent_ms": ms_tan, "adjoint_ms": ms_adj, "pullback_ms": ms_pb,
+            "forward_steps_per_s": steps / (ms_fwd * 1e-3), "tangent_steps_per_s": steps / (ms_tan * 1e-3),
+            "adjoint_steps_per_s": steps / (ms_adj * 1e-3),
+            "kappa_rms": float(lens[0].std().item()), "gamma_rms": float(lens[1:3].std().item()),
+            "omega_rms": float(lens[3].std().item()), "loss": float(((tan["xi"] - ref) ** 2).sum().item()),
+            "grad_phi0_rms": float(g0.std().item()), "gpu_launches": 5}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tree.free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -449,11 +502,12 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rays", type=int, default=0, help="trace a seeded subset of N rays (profiling only)")
-    ap.add_argument("--workload", default="amr", choices=["amr", "batched", "large"],
+    ap.add_argument("--workload", default="amr", choices=["amr", "batched", "large", "diff"],
                     help="amr: the headline benchmark; batched: 64 light cones (separate report)")
     ap.add_argument("--batched-scale", type=float, default=1.0)
     ap.add_argument("--large-n", type=int, default=0, help="coarse size of a reduced large run (0: 1024)")
     ap.add_argument("--large-nside", type=int, default=2048)
+    ap.add_argument("--diff-pix", type=int, default=1024)
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":
@@ -462,6 +516,8 @@ def main():
         run_batched(args, ws, rank)
     elif args.workload == "large":
         run_large(args, ws, rank)
+    elif args.workload == "diff":
+        run_diff(args, ws, rank)
     else:
         run_ours(args, ws, rank)
     if ws > 1:

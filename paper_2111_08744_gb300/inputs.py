@@ -784,3 +784,13 @@ def config_large_gpu(n: int = 1024, box: float = 2600.0, n_levels: int = 4, f1: 
                  ray_begin=np.array([0, dirs.shape[1]], dtype=np.int64), dirs=dirs, steps_per_cell=steps_per_cell,
                  phi0=None, detail=None)
     return w
+
+
+def config_diff(n_pix: int = 1024, n: int = 128, box: float = 1000.0, n_levels: int = 3, width_deg: float = 10.0,
+                z_max: float = 1.0, seed: int = 2114) -> Workload:
+    """Differentiation workload: the AMR generator at n^3 coarse cells in `box` (3 levels, two
+    slices), n_pix x n_pix rays on a tangent-plane grid of width_deg centred on (theta = 90 deg,
+    phi = 0) to z_max; the end-point loss is compared with the FLRW end points."""
+    w = config_amr(n=n, box=box, n_levels=n_levels, nside=1, z_max=z_max, seed=seed, name="diff")
+    dirs = gnomonic_patch(n_pix, n_pix, width_deg)
+    return with_rays(w, dirs, name=f"diff_{n}cube_L{n_levels}_{n_pix}x{n_pix}_z{z_max:g}")
