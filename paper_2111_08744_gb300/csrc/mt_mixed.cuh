@@ -58,6 +58,75 @@ __device__ __forceinline__ bool stage_coords(const DevField& F, const int* ib, c
   return inside;
 }
 
+// Per-ray staging of the last CIC neighbourhood in shared memory: the 8 corner records of
+// both bracketing slices (16 float4) and their key (level, slice, lower corner).  Consecutive
+// RK4 stages of a ray stay in one neighbourhood most of the time (a step moves 1/N of a cell), so
+// most stages read their records from shared memory instead of L1/L2, and skip the index work.
+struct LaneCache {
+  float4* rec;   // rec[j * stride] for j = 0..15 (corner-major, lanes interleaved: no bank conflicts)
+  int4* key;     // (level << 8 | slice, i0x, i0y, i0z); level -1: empty
+  int stride;
+};
+
+// CIC at level l (FP32) from finest-level integer coordinates; v as in cic_gather.
+__device__ __forceinline__ bool cic_int_cached(const DevField& F, int l, const int* ic, const float* fc, int s,
+                                               float* v, unsigned* err, const LaneCache& lc) {
+  const int sh = F.L - l;
+  const float inv = 1.0f / (float)(1 << sh);
+  int i0[3];
+  float f[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int ilev = ic[d] >> sh;
+    const float fl = ((float)(ic[d] & ((1 << sh) - 1)) + fc[d]) * inv;
+    if (fl >= 0.5f) {
+      i0[d] = ilev;
+      f[d] = fl - 0.5f;
+    } else {
+      i0[d] = ilev - 1;
+      f[d] = fl + 0.5f;
+    }
+  }
+  const int4 key = make_int4((l << 8) | s, i0[0], i0[1], i0[2]);
+  const int4 old = *lc.key;
+  const bool hit = old.x == key.x && old.y == key.y && old.z == key.z && old.w == key.w;
+  if (!hit) {
+    const long long i0l[3] = {i0[0], i0[1], i0[2]};
+    unsigned rows[8];
+    if (!cic_rows(F, l, i0l, rows, err)) return false;
+    const float4* rec = (const float4*)F.rec[l];
+    const int S = F.S;
+    const int s1 = (S > 1) ? s + 1 : s;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float4* rc = rec + (size_t)rows[c] * (size_t)S;
+      lc.rec[(2 * c) * lc.stride] = __ldg(rc + s);
+      lc.rec[(2 * c + 1) * lc.stride] = __ldg(rc + s1);
+    }
+    *lc.key = key;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float wx = (c & 1) ? f[0] : 1.0f - f[0];
+    const float wy = (c & 2) ? f[1] : 1.0f - f[1];
+    const float wz = (c & 4) ? f[2] : 1.0f - f[2];
+    const float w = wx * wy * wz;
+    const float4 r0 = lc.rec[(2 * c) * lc.stride];
+    const float4 r1 = lc.rec[(2 * c + 1) * lc.stride];
+    v[0] += w * r0.x;
+    v[1] += w * r0.y;
+    v[2] += w * r0.z;
+    v[3] += w * r0.w;
+    v[4] += w * r1.x;
+    v[5] += w * r1.y;
+    v[6] += w * r1.z;
+    v[7] += w * r1.w;
+  }
+  return true;
+}
+
 // CIC at level l (FP32) from finest-level integer coordinates; v as in cic_gather.
 __device__ __forceinline__ bool cic_int(const DevField& F, int l, const int* ic, const float* fc, int s, float* v,
                                         unsigned* err) {
@@ -111,7 +180,8 @@ struct MixedStep {
 // start and wave vector (k0, k).  *lf (if non-null) receives the most refined level.
 __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const MixedStep& B, double eta_step,
                                           const float* offx, float offe, float k0, const float* k, float* Kk0,
-                                          float* Kk, float* KI, float* Ks, int* lf, unsigned* err) {
+                                          float* Kk, float* KI, float* Ks, int* lf, unsigned* err,
+                                          const LaneCache* lc) {
   // background H(eta_step + offe)
   const float t = B.tb + offe * F.bg_inv_deta_f;
   const float ct = floorf(t);
@@ -150,8 +220,13 @@ __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const Mi
       }
       float v[8];
       int l = lfin;
-      for (; l >= 0; --l)
-        if (cic_int(F, l, ic, fc, s, v, err)) break;
+      if (lc) {
+        for (; l >= 0; --l)
+          if (cic_int_cached(F, l, ic, fc, s, v, err, *lc)) break;
+      } else {
+        for (; l >= 0; --l)
+          if (cic_int(F, l, ic, fc, s, v, err)) break;
+      }
       if (l < 0) return false;
       if (F.S == 1) {
         phi = v[0];
@@ -184,7 +259,8 @@ __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const Mi
 
 // One mixed-precision RK4 step; state and status conventions as ray_step.
 template <class RayStateT, class TraceArgsT>
-__device__ bool ray_step_mixed(const DevField& F, const TraceArgsT& A, RayStateT& r, unsigned* err) {
+__device__ bool ray_step_mixed(const DevField& F, const TraceArgsT& A, RayStateT& r, unsigned* err,
+                               const LaneCache* lc = nullptr) {
   if (r.n_steps == 0 && !(r.y[3] > r.eta_stop)) return true;
   if (r.n_steps >= A.max_steps) {
     r.status = MT_RAY_MAX_STEPS;
@@ -221,7 +297,7 @@ __device__ bool ray_step_mixed(const DevField& F, const TraceArgsT& A, RayStateT
     const float kst[3] = {ks[0] + offk[0], ks[1] + offk[1], ks[2] + offk[2]};
     float Kk0, Kk[3], KI, Ks;
     int lf = 0;
-    if (!rhs_mixed(F, grav, B, eta, offx, offe, kst0, kst, &Kk0, Kk, &KI, &Ks, st == 0 ? &lf : nullptr, err)) {
+    if (!rhs_mixed(F, grav, B, eta, offx, offe, kst0, kst, &Kk0, Kk, &KI, &Ks, st == 0 ? &lf : nullptr, err, lc)) {
       r.status = MT_RAY_LEFT_DOMAIN;
       return true;
     }

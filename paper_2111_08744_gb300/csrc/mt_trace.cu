@@ -32,6 +32,13 @@ __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCone
   const unsigned lane = threadIdx.x & 31u;
   const long long n = A.n_rays;
   const bool grav = A.gravity_on != 0;
+  // mixed path: per-ray CIC neighbourhood staged in shared memory (16 float4 + key per thread)
+  extern __shared__ float4 smem[];
+  LaneCache lc;
+  lc.rec = smem + threadIdx.x;
+  lc.key = (int4*)(smem + 16 * BS) + threadIdx.x;
+  lc.stride = BS;
+  const LaneCache* lcp = sizeof(T) == 4 ? &lc : nullptr;
   RayState r;
   long long ray = -1;
   bool exhausted = false;
@@ -48,6 +55,7 @@ __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCone
         if (id < n) {
           ray = id;
           ray_init<T>(F, C, dirs, n, ray, grav, r, err);
+          if (lcp) *lc.key = make_int4(-1, 0, 0, 0);
         } else {
           exhausted = true;
         }
@@ -56,7 +64,7 @@ __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCone
     const bool alive = ray >= 0;
     if (!__any_sync(0xffffffffu, alive)) break;
     if (alive) {
-      if (ray_step<T>(F, A, r, err)) {
+      if (ray_step<T>(F, A, r, err, lcp)) {
         ray_finish<T>(F, A, r, ray, n, O, err);
         ray = -1;
       }
@@ -64,12 +72,20 @@ __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCone
   }
 }
 
+// Dynamic shared memory of trace_kernel<T, BS>: the mixed path's per-thread neighbourhood cache.
+template <class T, int BS>
+constexpr size_t trace_smem() {
+  return sizeof(T) == 4 ? (size_t)BS * (16 * sizeof(float4) + sizeof(int4)) : 0;
+}
+
 template <class T, int BS>
 int blocks_per_sm() {
   static int cached = -1;
   if (cached < 0) {
+    const size_t sm = trace_smem<T, BS>();
+    if (sm > 48 * 1024) cudaFuncSetAttribute(trace_kernel<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<T, BS>, BS, 0) != cudaSuccess || b < 1) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<T, BS>, BS, sm) != cudaSuccess || b < 1) b = 1;
     cached = b;
   }
   return cached;
@@ -80,7 +96,7 @@ void launch_trace_bs(const mt_octree* tree, const DevCones& C, const double* dir
                      const TraceArgs& A, cudaStream_t stream) {
   int bps = blocks_per_sm<T, BS>();
   if (tree->launch_bps > 0 && tree->launch_bps < bps) bps = tree->launch_bps;
-  trace_kernel<T, BS><<<tree->num_sms * bps, BS, 0, stream>>>(tree->f, C, dirs, O, A, tree->ws);
+  trace_kernel<T, BS><<<tree->num_sms * bps, BS, trace_smem<T, BS>(), stream>>>(tree->f, C, dirs, O, A, tree->ws);
 }
 
 // Launch shape: the octree's configuration (mt_set_launch_config), default 128 threads and as

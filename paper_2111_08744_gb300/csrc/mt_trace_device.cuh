@@ -197,9 +197,10 @@ __device__ __forceinline__ bool ray_step_fp64(const DevField& F, const TraceArgs
 // One RK4 step of the trace kernels: FP64 fields integrate in FP64; FP32 fields use the
 // mixed-precision step (mt_mixed.cuh).
 template <class T>
-__device__ __forceinline__ bool ray_step(const DevField& F, const TraceArgs& A, RayState& r, unsigned* err) {
+__device__ __forceinline__ bool ray_step(const DevField& F, const TraceArgs& A, RayState& r, unsigned* err,
+                                         const LaneCache* lc = nullptr) {
   if constexpr (sizeof(T) == 4) {
-    return ray_step_mixed(F, A, r, err);
+    return ray_step_mixed(F, A, r, err, lc);
   } else {
     return ray_step_fp64<T>(F, A, r, err);
   }
