@@ -51,7 +51,7 @@ class _Level(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("n_cones", ctypes.c_int32), ("steps_per_cell", ctypes.c_int32), ("gravity_on", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("observer", ctypes.c_void_p), ("z_max", ctypes.c_void_p),
+                ("interp", ctypes.c_int32), ("observer", ctypes.c_void_p), ("z_max", ctypes.c_void_p),
                 ("ray_begin", ctypes.c_void_p), ("max_steps", ctypes.c_int64)]
 
 
@@ -79,7 +79,7 @@ def _load():
             lib.orc_sample.restype = ctypes.c_int
             lib.orc_sample.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Level), ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
-                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
             lib.orc_eta_stop.restype = ctypes.c_double
             lib.orc_eta_stop.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
             lib.orc_background.restype = None
@@ -96,7 +96,7 @@ def _ptr(a):
 class _Marshal:
     """Holds contiguous FP64 copies of a workload's arrays for the duration of a call."""
 
-    def __init__(self, w, levels=None, gravity_on=True, max_steps=10_000_000):
+    def __init__(self, w, levels=None, gravity_on=True, max_steps=10_000_000, interp=0):
         lv = levels if levels is not None else w.levels
         self.keep = []
         self.seta = np.ascontiguousarray(w.slice_eta, dtype=np.float64)
@@ -113,7 +113,7 @@ class _Marshal:
         self.obs = np.ascontiguousarray(w.observer, dtype=np.float64).reshape(-1, 3)
         self.zmax = np.ascontiguousarray(w.z_max, dtype=np.float64)
         self.begin = np.ascontiguousarray(w.ray_begin, dtype=np.int64)
-        self.params = _Params(int(self.obs.shape[0]), int(w.steps_per_cell), 1 if gravity_on else 0, 0,
+        self.params = _Params(int(self.obs.shape[0]), int(w.steps_per_cell), 1 if gravity_on else 0, int(interp),
                               _ptr(self.obs), _ptr(self.zmax), _ptr(self.begin), int(max_steps))
 
 
@@ -121,8 +121,18 @@ def default_threads() -> int:
     return max(1, os.cpu_count() or 1)
 
 
-def trace(w, dirs=None, levels=None, gravity_on=True, max_steps=10_000_000, n_threads=None, ray_begin=None):
+INTERP = {"cic": 0, "ngp": 1, "tsc": 2}
+
+
+def _interp(interp):
+    return INTERP[interp] if isinstance(interp, str) else int(interp)
+
+
+def trace(w, dirs=None, levels=None, gravity_on=True, max_steps=10_000_000, n_threads=None, ray_begin=None,
+          interp="cic"):
     """Trace rays of workload `w` (optionally other directions / a subset). Returns a dict of arrays.
+
+    interp: "cic" (Eq. 8), "ngp" (Eq. 7) or "tsc" (Eq. 9), each with the level fallback of Sect. 2.2.
 
     Besides the per-ray outputs of the method, "tie" is the smallest margin of any index
     decision along the ray: the distance (in cell units) of a floor() argument to the
@@ -130,7 +140,7 @@ def trace(w, dirs=None, levels=None, gravity_on=True, max_steps=10_000_000, n_th
     with a tie below ~1e-8 can take either side of a cell face under rounding alone.
     """
     lib = _load()
-    m = _Marshal(w, levels, gravity_on, max_steps)
+    m = _Marshal(w, levels, gravity_on, max_steps, _interp(interp))
     d = np.ascontiguousarray(w.dirs if dirs is None else dirs, dtype=np.float64)
     n = int(d.shape[1])
     if ray_begin is not None:
@@ -152,10 +162,10 @@ def trace(w, dirs=None, levels=None, gravity_on=True, max_steps=10_000_000, n_th
     return out
 
 
-def bundle_jacobian(w, dirs=None, eps=1e-7, screen=0, levels=None, gravity_on=True, n_threads=None):
+def bundle_jacobian(w, dirs=None, eps=1e-7, screen=0, levels=None, gravity_on=True, n_threads=None, interp="cic"):
     """Finite-beam distortion matrix (Eqs. 17-21) per central direction, [4, N] = A11, A12, A21, A22."""
     lib = _load()
-    m = _Marshal(w, levels, gravity_on)
+    m = _Marshal(w, levels, gravity_on, interp=_interp(interp))
     d = np.ascontiguousarray(w.dirs if dirs is None else dirs, dtype=np.float64)
     n = int(d.shape[1])
     if dirs is not None:
@@ -169,8 +179,8 @@ def bundle_jacobian(w, dirs=None, eps=1e-7, screen=0, levels=None, gravity_on=Tr
     return A
 
 
-def sample(w, pts, eta, levels=None):
-    """Interpolated (phi, grad[3], phi_eta, finest level, CIC level) at points [3, n]."""
+def sample(w, pts, eta, levels=None, interp="cic"):
+    """Interpolated (phi, grad[3], phi_eta, finest level, interpolation level) at points [3, n]."""
     lib = _load()
     m = _Marshal(w, levels)
     p = np.ascontiguousarray(pts, dtype=np.float64)
@@ -179,7 +189,7 @@ def sample(w, pts, eta, levels=None):
     phi, grad, pe = np.zeros(n), np.zeros((3, n)), np.zeros(n)
     lf, lc = np.zeros(n, dtype=np.int32), np.zeros(n, dtype=np.int32)
     rc = lib.orc_sample(ctypes.byref(m.grid), m.levels, _ptr(p), _ptr(e), n, _ptr(phi), _ptr(grad), _ptr(pe),
-                        _ptr(lf), _ptr(lc))
+                        _ptr(lf), _ptr(lc), _interp(interp))
     if rc != 0:
         raise RuntimeError(f"oracle sample failed with code {rc}")
     return phi, grad, pe, lf, lc

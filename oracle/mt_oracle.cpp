@@ -7,7 +7,7 @@
 // Plain, slow, obviously correct: every stage of every RK4 step re-derives the
 // cell indices from the position, looks each cell up by binary search in the
 // level's sorted key vector (the paper's sorted-vector octree, Sect. 3.1), and
-// evaluates the CIC weights of Eq. (8) corner by corner.  Compiled with
+// evaluates the weights of Eq. (8) (CIC; or Eq. 7, NGP, or Eq. 9, TSC) cell by cell.  Compiled with
 // -ffp-contract=off so every operation is a single IEEE-754 double operation.
 //
 // Conventions (c = 1, lengths and eta in h^-1 Mpc, phi = Phi/c^2):
@@ -50,7 +50,7 @@ struct orc_params {
   int32_t n_cones;
   int32_t steps_per_cell;
   int32_t gravity_on;
-  int32_t pad;
+  int32_t interp;           // 0: CIC, 1: NGP, 2: TSC (Sect. 2.2 weighting functions)
   const double* observer;   // [n_cones][3]
   const double* z_max;      // [n_cones]
   const int64_t* ray_begin; // [n_cones + 1]
@@ -142,9 +142,12 @@ struct Background {
   }
 };
 
+enum { INTERP_CIC = 0, INTERP_NGP = 1, INTERP_TSC = 2 };
+
 struct Field {
   double box;
   int nc, L, S;
+  int interp = INTERP_CIC;
   bool periodic;
   const double* seta;
   const orc_level* lv;
@@ -223,18 +226,74 @@ struct Field {
     }
     return true;
   }
+  // NGP (Eq. 7, Sect. 2.2): the records of the level-l cell containing the point.
+  bool ngp_level(int l, const double* u, double (*vals)[4]) const {
+    double s = std::ldexp(1.0, l);
+    int64_t c[3];
+    for (int d = 0; d < 3; ++d) c[d] = (int64_t)std::floor(u[d] * s);
+    int64_t row = find(l, c[0], c[1], c[2]);
+    if (row < 0) return false;
+    const double* rec = lv[l].records + (size_t)row * (size_t)S * 4;
+    for (int sl = 0; sl < S; ++sl)
+      for (int q = 0; q < 4; ++q) vals[sl][q] = rec[sl * 4 + q];
+    return true;
+  }
+  // W_TSC, Eq. (9): 3/4 - r^2 for |r| < 1/2, (3/2 - |r|)^2 / 2 for 1/2 <= |r| < 3/2, else 0
+  static double w_tsc(double r) {
+    double a = std::fabs(r);
+    if (a < 0.5) return 0.75 - r * r;
+    if (a < 1.5) return 0.5 * (1.5 - a) * (1.5 - a);
+    return 0.0;
+  }
+  // TSC at level l: the cell containing the point and its 26 neighbours (27 cells, the same
+  // for every position inside that cell); false when one of them is absent.
+  bool tsc_level(int l, const double* u, double (*vals)[4], double* tie = nullptr) const {
+    double s = std::ldexp(1.0, l);
+    double U[3];
+    int64_t c[3];
+    for (int d = 0; d < 3; ++d) {
+      U[d] = u[d] * s;
+      c[d] = (int64_t)std::floor(U[d]);
+      note_tie(U[d], tie);
+    }
+    int64_t rows[27];
+    for (int m = 0; m < 27; ++m) {
+      int o[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
+      rows[m] = find(l, c[0] + o[0], c[1] + o[1], c[2] + o[2]);
+      if (rows[m] < 0) return false;
+    }
+    for (int sl = 0; sl < S; ++sl)
+      for (int q = 0; q < 4; ++q) vals[sl][q] = 0.0;
+    for (int m = 0; m < 27; ++m) {
+      int o[3] = {m % 3 - 1, (m / 3) % 3 - 1, m / 9 - 1};
+      double w = 1.0;
+      for (int d = 0; d < 3; ++d) {
+        double centre = (double)(c[d] + o[d]) + 0.5;
+        w = w * w_tsc(U[d] - centre);
+      }
+      const double* rec = lv[l].records + (size_t)rows[m] * (size_t)S * 4;
+      for (int sl = 0; sl < S; ++sl)
+        for (int q = 0; q < 4; ++q) vals[sl][q] += w * rec[sl * 4 + q];
+    }
+    return true;
+  }
   // Interpolated phi, grad phi and d phi/d eta at (u, eta), with the level fallback of
   // Sect. 2.2 (start at the most refined level containing the photon, go coarser while a
-  // neighbour is missing).  Time: linear in eta between the bracketing slices.
-  // Returns false when even level 0 lacks neighbours (edge of a non-periodic domain).
+  // neighbour is missing; NGP takes the containing cell itself).  Time: linear in eta
+  // between the bracketing slices.  Returns false when even level 0 lacks neighbours (edge
+  // of a non-periodic domain).
   bool sample(const double* u, double eta, double* phi, double* grad, double* phi_eta, int* lev_used,
               double* tie = nullptr) const {
     int lf = finest(u, tie);
     if (lf < 0) return false;
     double vals[64][4];
     int l = lf;
-    for (; l >= 0; --l)
-      if (cic_level(l, u, vals, tie)) break;
+    for (; l >= 0; --l) {
+      bool ok = interp == INTERP_NGP ? ngp_level(l, u, vals)
+                : interp == INTERP_TSC ? tsc_level(l, u, vals, tie)
+                                       : cic_level(l, u, vals, tie);
+      if (ok) break;
+    }
     if (l < 0) return false;
     if (lev_used) *lev_used = l;
     if (S == 1) {
@@ -375,6 +434,7 @@ Tracer make_tracer(const orc_grid* g, const orc_level* lv, const double* bg, int
   t.f.periodic = g->periodic != 0;
   t.f.seta = g->slice_eta;
   t.f.lv = lv;
+  t.f.interp = p->interp;
   t.bg.tab = bg;
   t.bg.n = bg_n;
   t.N = p->steps_per_cell;
@@ -433,11 +493,13 @@ void orc_background(const double* bg, int bg_n, const double* eta, int64_t n, do
 
 // Interpolated field at arbitrary points (tests of the lookup and of Eq. 8).
 int orc_sample(const orc_grid* g, const orc_level* lv, const double* pts /*[3][n]*/, const double* eta, int64_t n,
-               double* phi, double* grad /*[3][n]*/, double* phi_eta, int32_t* level_finest, int32_t* level_cic) {
+               double* phi, double* grad /*[3][n]*/, double* phi_eta, int32_t* level_finest, int32_t* level_cic,
+               int interp) {
   if (!keys_sorted(g, lv)) return 4;
+  if (interp < INTERP_CIC || interp > INTERP_TSC) return 5;
   Field f;
   f.box = g->box; f.nc = g->n_coarse; f.L = g->n_levels; f.S = g->n_slices;
-  f.periodic = g->periodic != 0; f.seta = g->slice_eta; f.lv = lv;
+  f.periodic = g->periodic != 0; f.seta = g->slice_eta; f.lv = lv; f.interp = interp;
   for (int64_t i = 0; i < n; ++i) {
     double x[3] = {pts[i], pts[n + i], pts[2 * n + i]}, u[3], gr[3] = {0, 0, 0}, p = 0, pe = 0;
     f.coarse_coords(x, u);
@@ -454,6 +516,7 @@ int orc_sample(const orc_grid* g, const orc_level* lv, const double* pts /*[3][n
 int orc_trace(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n, const orc_params* p,
               const double* dirs /*[3][N]*/, int64_t n_rays, orc_out* o, int n_threads) {
   if (!keys_sorted(g, lv)) return 4;
+  if (p->interp < INTERP_CIC || p->interp > INTERP_TSC) return 5;
   Tracer t = make_tracer(g, lv, bg, bg_n, p);
   std::vector<double> es(p->n_cones);
   for (int c = 0; c < p->n_cones; ++c) es[c] = t.bg.eta_stop(p->z_max[c]);
@@ -501,6 +564,7 @@ int orc_trace(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n
 int orc_bundle(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n, const orc_params* p,
                const double* dirs, int64_t n_rays, double eps, int screen, double* A /*[4][N]*/, int n_threads) {
   if (!keys_sorted(g, lv)) return 4;
+  if (p->interp < INTERP_CIC || p->interp > INTERP_TSC) return 5;
   Tracer t = make_tracer(g, lv, bg, bg_n, p);
   std::vector<double> es(p->n_cones);
   for (int c = 0; c < p->n_cones; ++c) es[c] = t.bg.eta_stop(p->z_max[c]);
