@@ -76,6 +76,10 @@ def _load():
             lib.orc_bundle.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Level), ctypes.c_void_p, ctypes.c_int,
                                        ctypes.POINTER(_Params), ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
                                        ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+            lib.orc_infinitesimal.restype = ctypes.c_int
+            lib.orc_infinitesimal.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Level), ctypes.c_void_p,
+                                              ctypes.c_int, ctypes.POINTER(_Params), ctypes.c_void_p, ctypes.c_int64,
+                                              ctypes.c_void_p, ctypes.c_int]
             lib.orc_sample.restype = ctypes.c_int
             lib.orc_sample.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Level), ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
@@ -176,6 +180,26 @@ def bundle_jacobian(w, dirs=None, eps=1e-7, screen=0, levels=None, gravity_on=Tr
                         _ptr(d), n, float(eps), int(screen), _ptr(A), int(n_threads or default_threads()))
     if rc != 0:
         raise RuntimeError(f"oracle bundle failed with code {rc}")
+    return A
+
+
+def infinitesimal_jacobian(w, dirs=None, levels=None, gravity_on=True, n_threads=None, interp="cic"):
+    """Infinitesimal-beam distortion matrix, Eq. (12) with the Hessian of Eq. (13) and the screen
+    projection of Eqs. (14)-(16) (e_1 = e_phi, e_2 = -e_theta), integrated by the trapezoidal rule
+    over the step points of each traced ray.  gravity_on=False integrates along FLRW trajectories
+    (the Born approximation).  Returns [4, N] = A11, A12, A21, A22."""
+    lib = _load()
+    m = _Marshal(w, levels, gravity_on, interp=_interp(interp))
+    d = np.ascontiguousarray(w.dirs if dirs is None else dirs, dtype=np.float64)
+    n = int(d.shape[1])
+    if dirs is not None:
+        m.begin = np.array([0, n], dtype=np.int64)
+        m.params.ray_begin = _ptr(m.begin)
+    A = np.zeros((4, n))
+    rc = lib.orc_infinitesimal(ctypes.byref(m.grid), m.levels, _ptr(m.bg), int(m.bg.shape[0]), ctypes.byref(m.params),
+                               _ptr(d), n, _ptr(A), int(n_threads or default_threads()))
+    if rc != 0:
+        raise RuntimeError(f"oracle infinitesimal beam failed with code {rc}")
     return A
 
 

@@ -346,15 +346,81 @@ struct Tracer {
     return true;
   }
 
+  // Infinitesimal-beam integrand at a point of the ray (Sect. 2.3.1): the Cartesian Hessian of
+  // phi by Eq. (13), central differences of the interpolated grad phi with the step h = size of
+  // the most refined cell containing the point (only i <= j is computed, d_i d_j = d_j d_i), then
+  // its components on the screen of the photon's angular position (phi_a, theta_a) seen from the
+  // observer, Eqs. (14)-(16), written for e_1 = e_phi and e_2 = -e_theta (the screen basis of the
+  // finite beams, Eq. 21).  fo[0] = d1 d1 phi, fo[1] = d2 d2 phi, fo[2] = d1 d2 phi.  False if a
+  // sample point lies outside a non-periodic domain.
+  bool screen_hessian(const double* x, double eta, const double* xo, double* fo) const {
+    double u[3];
+    f.coarse_coords(x, u);
+    int lf = f.finest(u);
+    if (lf < 0) return false;
+    double h = f.dx(lf);
+    double H[3][3];
+    for (int i = 0; i < 3; ++i) {
+      double gp[3], gm[3], up[3], um[3], phi, pe;
+      double xp[3] = {x[0], x[1], x[2]}, xm[3] = {x[0], x[1], x[2]};
+      xp[i] += h;
+      xm[i] -= h;
+      f.coarse_coords(xp, up);
+      f.coarse_coords(xm, um);
+      if (!f.sample(up, eta, &phi, gp, &pe, nullptr)) return false;
+      if (!f.sample(um, eta, &phi, gm, &pe, nullptr)) return false;
+      for (int j = i; j < 3; ++j) H[i][j] = (gp[j] - gm[j]) / (2.0 * h);
+    }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < i; ++j) H[i][j] = H[j][i];
+    double v[3] = {x[0] - xo[0], x[1] - xo[1], x[2] - xo[2]};
+    double rr = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double ph = std::atan2(v[1], v[0]);
+    double th = std::acos(std::max(-1.0, std::min(1.0, v[2] / rr)));
+    double sp = std::sin(ph), cp = std::cos(ph), st = std::sin(th), ct = std::cos(th);
+    double Hxx = H[0][0], Hyy = H[1][1], Hzz = H[2][2], Hxy = H[0][1], Hxz = H[0][2], Hyz = H[1][2];
+    fo[0] = sp * sp * Hxx + cp * cp * Hyy - 2.0 * sp * cp * Hxy;                                  // Eq. (14)
+    fo[1] = cp * cp * ct * ct * Hxx + sp * sp * ct * ct * Hyy + st * st * Hzz + 2.0 * sp * cp * ct * ct * Hxy -
+           2.0 * sp * st * ct * Hyz - 2.0 * cp * st * ct * Hxz;                                  // Eq. (15)
+    fo[2] = -(ct * cp * sp * (Hyy - Hxx) + (cp * cp - sp * sp) * ct * Hxy + sp * st * Hxz - cp * st * Hyz);  // -Eq. (16)
+    return true;
+  }
+
   struct Result {
     double y[10];
     double lambda, phi_o, phi_s;
     int n_steps, level, status;
     double tie;
+    double A[4];   // infinitesimal-beam distortion matrix (when requested): A11, A12, A21, A22
   };
 
-  Result trace(const double* xo, const double* n, double eta_stop) const {
+  // Eq. (12) along the traced ray by the trapezoidal rule over its step points, split as
+  // int chi f dchi - (1/chi_s) int chi^2 f dchi so that chi_s (known at the end) factors out.
+  struct InfBeam {
+    double I1[3] = {0, 0, 0}, I2[3] = {0, 0, 0};
+    double prev_chi = 0.0, prev_f[3] = {0, 0, 0};
+    void add(double chi, const double* f) {
+      double dchi = chi - prev_chi;
+      for (int c = 0; c < 3; ++c) {
+        I1[c] += 0.5 * (prev_chi * prev_f[c] + chi * f[c]) * dchi;
+        I2[c] += 0.5 * (prev_chi * prev_chi * prev_f[c] + chi * chi * f[c]) * dchi;
+        prev_f[c] = f[c];
+      }
+      prev_chi = chi;
+    }
+    void matrix(double* A) const {
+      double m[3];
+      for (int c = 0; c < 3; ++c) m[c] = prev_chi > 0.0 ? I1[c] - I2[c] / prev_chi : 0.0;
+      A[0] = 1.0 - 2.0 * m[0];
+      A[1] = -2.0 * m[2];
+      A[2] = -2.0 * m[2];
+      A[3] = 1.0 - 2.0 * m[1];
+    }
+  };
+
+  Result trace(const double* xo, const double* n, double eta_stop, bool inf_beam = false) const {
     Result r;
+    InfBeam ib;
     double* y = r.y;
     double eta_o = bg.tab[4 * (bg.n - 1)];
     double phi_o = 0.0;
@@ -407,9 +473,17 @@ struct Tracer {
       bool finite = true;
       for (int i = 0; i < 10; ++i) finite = finite && std::isfinite(y[i]);
       if (!finite) { r.status = ST_NONFINITE; break; }
+      if (inf_beam) {
+        double fv[3] = {0.0, 0.0, 0.0};
+        double d[3] = {y[0] - xo[0], y[1] - xo[1], y[2] - xo[2]};
+        double chi = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (!screen_hessian(y, y[3], xo, fv)) fv[0] = fv[1] = fv[2] = 0.0;
+        ib.add(chi, fv);
+      }
       if (last) break;
     }
   done:
+    ib.matrix(r.A);
     r.phi_s = 0.0;
     r.level = -1;
     {
@@ -551,6 +625,25 @@ int orc_trace(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n
     o->level[i] = r.level;
     o->status[i] = r.status;
     if (o->tie) o->tie[i] = r.tie;
+  });
+  return 0;
+}
+
+// Infinitesimal-beam distortion matrix, Eq. (12) with Eqs. (13)-(16), integrated along each
+// traced ray (trapezoidal rule over the step points); with gravity off the rays are FLRW
+// trajectories: the Born approximation of Sect. 2.3.1.  A: [4][N] = A11, A12, A21, A22.
+int orc_infinitesimal(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n, const orc_params* p,
+                      const double* dirs, int64_t n_rays, double* A, int n_threads) {
+  if (!keys_sorted(g, lv)) return 4;
+  if (p->interp < INTERP_CIC || p->interp > INTERP_TSC) return 5;
+  Tracer t = make_tracer(g, lv, bg, bg_n, p);
+  std::vector<double> es(p->n_cones);
+  for (int c = 0; c < p->n_cones; ++c) es[c] = t.bg.eta_stop(p->z_max[c]);
+  parallel_for(n_rays, n_threads, [&](int64_t i) {
+    int c = cone_of(p, i);
+    double n[3] = {dirs[i], dirs[n_rays + i], dirs[2 * n_rays + i]};
+    Tracer::Result r = t.trace(p->observer + 3 * c, n, es[c], true);
+    for (int q = 0; q < 4; ++q) A[q * n_rays + i] = r.A[q];
   });
   return 0;
 }
