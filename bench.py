@@ -32,6 +32,34 @@ if ROOT not in sys.path:
 METRIC = "RK4 geodesic steps/s and rays/s to z=1 on AMR field; % of HBM roofline"
 UNIT = "rays/s"
 FIELD_BYTES_PER_STEP = 4 * 8 * 16 * 2   # 4 stages x 8 CIC records x 16 B (float4) x 2 bracketing slices
+# the same per interpolation scheme: NGP reads 1 cell per stage, CIC 8, TSC 27 (Eqs. 7-9)
+FIELD_BYTES_BY_SCHEME = {"ngp": 4 * 1 * 16 * 2, "cic": FIELD_BYTES_PER_STEP, "tsc": 4 * 27 * 16 * 2}
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one full launch of
+# trace_kernel<float> on the benchmark workload, from one single-pass ncu capture, with the
+# SHA-256 of the kernel's sources at capture time: reported only while they are unchanged.
+TRACE_KERNEL_SOURCES = ["include/mt.h", "paper_2111_08744_gb300/csrc/mt_internal.cuh",
+                        "paper_2111_08744_gb300/csrc/mt_mixed.cuh", "paper_2111_08744_gb300/csrc/mt_trace_device.cuh",
+                        "paper_2111_08744_gb300/csrc/mt_trace.cu"]
+NCU_TRAFFIC = {"bytes_per_launch": 69.68e9 + 1.20e9,
+               "sources_sha256": "66ced4355cb8ef0fe8d5bc1c6f3adbb75ae53785d32c0e5d78d3c32e1f3206a7"}
+
+
+def trace_kernel_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in TRACE_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(rel.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """ncu DRAM bytes of one trace launch, or None once the kernel changed since the capture."""
+    if NCU_TRAFFIC["sources_sha256"] and NCU_TRAFFIC["sources_sha256"] == trace_kernel_sha256():
+        return NCU_TRAFFIC["bytes_per_launch"]
+    return None
 
 
 def workload_config(w):
@@ -138,7 +166,7 @@ def rank_workload(w, rank, ws):
     return dataclasses.replace(w, observer=obs)
 
 
-def oracle_sample(w, budget_s=15.0):
+def oracle_sample(w, budget_s=15.0, interp="cic"):
     """Time the CPU oracle on a bounded, seeded sample of the rays; returns (rays/s, n, threads, secs)."""
     import oracle
     threads = oracle.default_threads()
@@ -147,7 +175,7 @@ def oracle_sample(w, budget_s=15.0):
     while True:
         idx = np.sort(rng.choice(w.n_rays, size=n, replace=False))
         t0 = time.perf_counter()
-        oracle.trace(w, dirs=w.dirs[:, idx], n_threads=threads)
+        oracle.trace(w, dirs=w.dirs[:, idx], n_threads=threads, interp=interp)
         dt = time.perf_counter() - t0
         if dt > budget_s / 4 or n >= w.n_rays:
             return n / dt, n, threads, dt
@@ -162,7 +190,7 @@ def run_reference(args, ws, rank):
     w = I.cached(I.config_amr)
     vals = []
     for i in range(args.warmup + args.steps):
-        v, n, threads, dt = oracle_sample(w, budget_s=args.ref_budget)
+        v, n, threads, dt = oracle_sample(w, budget_s=args.ref_budget, interp=args.interp)
         if i >= args.warmup:
             vals.append((v, n, dt))
     value = float(np.mean([v for v, _, _ in vals]))
@@ -170,7 +198,7 @@ def run_reference(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean([d for _, _, d in vals]) * 1e3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(w),
+            "config": dict(workload_config(w), interp=args.interp),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.default_threads(),
                              "kind": "oracle", "sample": f"{n} seeded rays of the 786,432 per step, FP64 field"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -194,7 +222,7 @@ def run_ours(args, ws, rank):
     stream = torch.cuda.current_stream()
     levels32 = I.fp32_levels(w)
     tree = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, levels32, w.bg, "fp32")
-    params = B.TraceParams.from_workload(w)
+    params = B.TraceParams.from_workload(w, interp=args.interp)
     n = w.n_rays
     dirs = torch.from_numpy(w.dirs).to(dev)
     out = B.alloc_outputs(n, dev)
@@ -258,19 +286,21 @@ def run_ours(args, ws, rank):
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = FIELD_BYTES_PER_STEP * total_steps / (ms * 1e-3) / 1e9
+    field_bytes = FIELD_BYTES_BY_SCHEME[args.interp]
+    achieved = field_bytes * total_steps / (ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-            "traffic": None, "kernel": "trace_kernel<float>",
-            "algorithmic_bytes_per_rk4_step": FIELD_BYTES_PER_STEP, "rk4_steps_per_launch": total_steps,
+            "traffic": measured_traffic() if (args.rays == 0 and args.interp == "cic") else None,
+            "kernel": "trace_kernel<float>",
+            "algorithmic_bytes_per_rk4_step": field_bytes, "rk4_steps_per_launch": total_steps,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, ns, threads, dt = oracle_sample(w, budget_s=args.ref_budget)
+        v, ns, threads, dt = oracle_sample(w, budget_s=args.ref_budget, interp=args.interp)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{ns} seeded rays of the 786,432 ({dt:.1f} s of FP64 oracle work on {threads} threads)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 state / f32 field", "data": "synthetic", "config": workload_config(w),
+            "dtype": "f64 state / f32 field", "data": "synthetic", "config": dict(workload_config(w), interp=args.interp),
             "steps_per_s": steps_per_s, "rk4_steps_per_step": total_steps,
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -417,6 +447,26 @@ def run_large(args, ws, rank):
     status = torch.bincount(out["status"].long(), minlength=4).tolist()
     levels = torch.bincount(out["level"].long() + 1, minlength=6).tolist()
     ms = float(np.mean(ts))
+    tangent = None
+    if args.large_tangent:
+        # the distortion matrix on every ray: one forward-mode pass (mixed tangent step)
+        del out
+        torch.cuda.empty_cache()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        res = B.trace_rays_adjoint(tree, params, dirs, jacobian=True, lensing=True)
+        b.record()
+        torch.cuda.synchronize()
+        tms = a.elapsed_time(b)
+        tsteps = int(res["n_steps"].sum().item())
+        lens = res["lens"]
+        ok = res["status"] == 0
+        tangent = {"ms": tms, "rays_per_s": n / (tms * 1e-3), "rk4_steps_per_s": tsteps / (tms * 1e-3),
+                   "same_steps_as_trace": tsteps == steps, "device_status": tree.device_status(),
+                   "rms_kappa": float(lens[0][ok].pow(2).mean().sqrt()),
+                   "rms_gamma": float((lens[1][ok].pow(2) + lens[2][ok].pow(2)).mean().sqrt()),
+                   "rms_omega": float(lens[3][ok].pow(2).mean().sqrt())}
+        del res
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -435,6 +485,8 @@ def run_large(args, ws, rank):
                          "traffic": None, "kernel": "trace_kernel<float>"},
             "generation_s": t_gen, "build_s": t_build, "device_status": st, "ray_status_counts": status,
             "end_level_counts": levels[1:], "clocks": ck, "step_ms_all": ts, "gpu_launches": args.steps}
+    if tangent is not None:
+        line["distortion_matrix"] = tangent
     if rank == 0:
         print(json.dumps(line), flush=True)
     tree.free()
@@ -477,6 +529,20 @@ def run_diff(args, ws, rank):
                                                      dL_dxi=dxi, checkpoint_every=64))
     g0, ms_pb = timed(lambda: B.pullback_coarse_phi(tree, adj["dL_drec"], w.slice_weight, w.n_coarse))
     lens = tan["lens"]
+    # the same rays on the FP32 copy of the records: mixed trace and mixed tangent step
+    del adj
+    tree32 = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, I.fp32_levels(w), w.bg, "fp32")
+    B.trace_rays(tree32, params, dirs)
+    out32, ms_fwd32 = timed(lambda: B.trace_rays(tree32, params, dirs))
+    tan32, ms_tan32 = timed(lambda: B.trace_rays_adjoint(tree32, params, dirs, jacobian=True, lensing=True))
+    dA = (tan32["jac"] - tan["jac"]).abs()
+    dk = (tan32["lens"][0] - lens[0]).abs()
+    steps32 = int(out32["n_steps"].sum().item())
+    mixed = {"forward_ms": ms_fwd32, "tangent_ms": ms_tan32, "forward_steps_per_s": steps32 / (ms_fwd32 * 1e-3),
+             "tangent_steps_per_s": steps32 / (ms_tan32 * 1e-3), "jac_abs_diff_vs_fp64_max": float(dA.max()),
+             "jac_abs_diff_vs_fp64_median": float(dA.median()), "kappa_abs_diff_median": float(dk.median()),
+             "kappa_abs_diff_p99": float(torch.quantile(dk[:1 << 20], 0.99))}
+    tree32.free()
     line = {"metric": "differentiable ray tracing: forward, distortion matrix and gradient time",
             "value": n / (ms_tan * 1e-3), "unit": "rays/s (distortion matrix)", "n_gpus": ws,
             "steps": 1, "warmup": 1, "ms_per_step": ms_tan, "higher_is_better": True, "scaling": "weak",
@@ -487,7 +553,7 @@ def run_diff(args, ws, rank):
             "adjoint_steps_per_s": steps / (ms_adj * 1e-3),
             "kappa_rms": float(lens[0].std().item()), "gamma_rms": float(lens[1:3].std().item()),
             "omega_rms": float(lens[3].std().item()), "loss": float(((tan["xi"] - ref) ** 2).sum().item()),
-            "grad_phi0_rms": float(g0.std().item()), "gpu_launches": 5}
+            "grad_phi0_rms": float(g0.std().item()), "mixed_fp32_field": mixed, "gpu_launches": 8}
     if rank == 0:
         print(json.dumps(line), flush=True)
     tree.free()
@@ -507,7 +573,11 @@ def main():
     ap.add_argument("--batched-scale", type=float, default=1.0)
     ap.add_argument("--large-n", type=int, default=0, help="coarse size of a reduced large run (0: 1024)")
     ap.add_argument("--large-nside", type=int, default=2048)
+    ap.add_argument("--large-tangent", action="store_true",
+                    help="large workload: also time the distortion-matrix pass on every ray")
     ap.add_argument("--diff-pix", type=int, default=1024)
+    ap.add_argument("--interp", default="cic", choices=["cic", "ngp", "tsc"],
+                    help="amr workload: interpolation scheme (Sect. 2.2; the benchmark line is CIC)")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":

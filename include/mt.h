@@ -120,6 +120,18 @@ mt_status mt_build_octree(const mt_grid_desc* grid, const mt_level_data* levels,
                           int32_t bg_n, void* stream, mt_octree** out);
 
 /*
+ * Interpolation of phi and grad phi at the photon (Sect. 2.2, Eqs. 7-9), each with the level
+ * fallback of Sect. 2.2: start at the most refined level containing the photon and go one level
+ * coarser while one of the cells the scheme needs is absent.
+ *   NGP: the containing cell itself (no fallback needed);
+ *   CIC: the 8 cells around the point, trilinear weights prod(1 - |r_i|);
+ *   TSC: the containing cell and its 26 neighbours (the same 27 cells anywhere inside it),
+ *        weights prod W_TSC(r_i), W_TSC = 3/4 - r^2 (|r| < 1/2), (3/2 - |r|)^2 / 2 (< 3/2).
+ * The reverse mode of mt_trace_rays_adjoint (dL_dxi) supports CIC only.
+ */
+typedef enum { MT_INTERP_CIC = 0, MT_INTERP_NGP = 1, MT_INTERP_TSC = 2 } mt_interp;
+
+/*
  * Trace parameters.  Rays [ray_begin[c], ray_begin[c+1]) belong to cone c
  * with observer observer[c] at eta_o and stop on the iso-eta surface
  * eta_stop(c) = eta(a = 1 / (1 + z_max[c])) (Sect. 2.4 stop criterion, here
@@ -129,7 +141,8 @@ typedef struct {
   int32_t n_cones;          /* 1 .. MT_MAX_CONES */
   int32_t steps_per_cell;   /* N >= 1 (Sect. 2.2; 4 in common settings) */
   int32_t gravity_on;       /* 0: phi = 0 (FLRW / Born trajectories, Sect. 2.2), 1: full equations */
-  int32_t pad;
+  int32_t interp;           /* weighting function of Sect. 2.2: MT_INTERP_CIC (0, Eq. 8),
+                               MT_INTERP_NGP (Eq. 7) or MT_INTERP_TSC (Eq. 9) */
   const double* observer;   /* host [n_cones][3] */
   const double* z_max;      /* host [n_cones], >= 0 */
   const int64_t* ray_begin; /* host [n_cones + 1], ray_begin[0] = 0, non-decreasing */
@@ -208,8 +221,11 @@ mt_status mt_trace_rays(const mt_octree* tree, const mt_trace_params* params, co
  * counts each ray's steps, allocates a temporary checkpoint buffer (8 doubles per
  * checkpoint), runs the sweep and frees it.  Rays that do not end with MT_RAY_OK add nothing.
  *
- * Both modes integrate the ray in FP64 arithmetic (records of the octree's precision) and
- * write the ray outputs `out` (NULL pointers skip an output) of that integration.
+ * Forward mode integrates each ray as mt_trace_rays does: FP64 arithmetic on an FP64 octree;
+ * on an FP32 octree the mixed step (FP32 stages, FP64 state) with FP32 stage derivatives and an
+ * FP64 tangent state.  Reverse mode integrates in FP64 arithmetic (records of the octree's
+ * precision) and supports MT_INTERP_CIC only (others: MT_ERR_UNSUPPORTED).  Both write the ray
+ * outputs `out` (NULL pointers skip an output) of their integration.
  * Errors: as mt_trace_rays; MT_ERR_INVALID_ARG if neither mode is requested or reverse-mode
  * arguments are incomplete; MT_ERR_OOM if the checkpoint buffer cannot be allocated.
  */
@@ -217,6 +233,25 @@ mt_status mt_trace_rays_adjoint(const mt_octree* tree, const mt_trace_params* pa
                                 int64_t n_rays, const mt_ray_out* out, double* jac, double* lens,
                                 const double* dL_dxi, double* const* dL_drec, int32_t checkpoint_every,
                                 void* stream);
+
+/*
+ * mt_trace_rays_lensing -- the infinitesimal-beam distortion matrix of Sect. 2.3.1 along each
+ * traced ray (Eq. 12):
+ *   A_ab = delta_ab - 2 int_0^chi_s dchi (chi_s - chi) chi / chi_s  d_a d_b phi(eta(chi), x(chi)),
+ * the Cartesian Hessian of phi from central differences of the interpolated grad phi with the
+ * step h = size of the most refined cell containing the photon (Eq. 13; d_i d_j = d_j d_i), its
+ * screen components at the photon's angular position seen from the observer (Eqs. 14-16, on the
+ * basis e_1 = e_phi, e_2 = -e_theta also used by the finite beams and mt_trace_rays_adjoint), and
+ * the trapezoidal rule over the ray's step points (chi = |x - x_o|).  A is symmetric (no
+ * rotation).  With params->gravity_on = 0 the rays follow FLRW trajectories: the Born
+ * approximation of Sect. 2.3.1.  The rays advance exactly as in mt_trace_rays (same step, same
+ * precision rules) and `out` receives their outputs.
+ * jac: device [4][N] = A11, A12, A21, A22; lens: device [5][N] = kappa, gamma_1, gamma_2,
+ * omega (= 0), det A (= 1/mu); at least one non-NULL.  Asynchronous on `stream`.
+ * Errors: as mt_trace_rays; MT_ERR_INVALID_ARG if jac and lens are both NULL.
+ */
+mt_status mt_trace_rays_lensing(const mt_octree* tree, const mt_trace_params* params, const double* dirs,
+                                int64_t n_rays, const mt_ray_out* out, double* jac, double* lens, void* stream);
 
 /*
  * mt_pullback_coarse_phi -- dL/dphi_0 on the coarse grid from record cotangents dL_drec

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libmt.so")
 MT_OK, MT_ERR_INVALID_ARG, MT_ERR_OOM, MT_ERR_CUDA, MT_ERR_NOT_FULL_TREE, MT_ERR_TIMEOUT, MT_ERR_OOB, \
     MT_ERR_UNSUPPORTED = range(8)
 MT_FIELD_FP64, MT_FIELD_FP32 = 0, 1
+MT_INTERP_CIC, MT_INTERP_NGP, MT_INTERP_TSC = 0, 1, 2
 MT_RAY_OK, MT_RAY_LEFT_DOMAIN, MT_RAY_MAX_STEPS, MT_RAY_NONFINITE = 0, 1, 2, 3
 MT_HOST, MT_DEVICE_COPY, MT_DEVICE_BORROW = 0, 1, 2
 MT_MAX_LEVELS, MT_MAX_SLICES, MT_MAX_CONES, MT_NOALLOC_MAX_CONES = 8, 16, 256, 4096
@@ -43,7 +44,7 @@ class mt_level_data(ctypes.Structure):
 
 class mt_trace_params(ctypes.Structure):
     _fields_ = [("n_cones", ctypes.c_int32), ("steps_per_cell", ctypes.c_int32), ("gravity_on", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("observer", ctypes.c_void_p), ("z_max", ctypes.c_void_p),
+                ("interp", ctypes.c_int32), ("observer", ctypes.c_void_p), ("z_max", ctypes.c_void_p),
                 ("ray_begin", ctypes.c_void_p), ("max_steps", ctypes.c_int64)]
 
 
@@ -80,6 +81,9 @@ def load():
         lib.mt_trace_rays_adjoint.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64,
                                               ctypes.POINTER(mt_ray_out), P, P, P, ctypes.POINTER(P),
                                               ctypes.c_int32, P]
+        lib.mt_trace_rays_lensing.restype = ctypes.c_int
+        lib.mt_trace_rays_lensing.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64,
+                                              ctypes.POINTER(mt_ray_out), P, P, P]
         lib.mt_pullback_coarse_phi.restype = ctypes.c_int
         lib.mt_pullback_coarse_phi.argtypes = [P, ctypes.POINTER(P), P, P, P]
         lib.mt_trace_rays_noalloc.restype = ctypes.c_int
@@ -138,6 +142,10 @@ def mt_trace_rays(tree, params, dirs, n_rays, out, stream):
 def mt_trace_rays_adjoint(tree, params, dirs, n_rays, out, jac, lens, dL_dxi, dL_drec, checkpoint_every, stream):
     return load().mt_trace_rays_adjoint(tree, params, dirs, n_rays, out, jac, lens, dL_dxi, dL_drec,
                                         checkpoint_every, stream)
+
+
+def mt_trace_rays_lensing(tree, params, dirs, n_rays, out, jac, lens, stream):
+    return load().mt_trace_rays_lensing(tree, params, dirs, n_rays, out, jac, lens, stream)
 
 
 def mt_trace_rays_noalloc(tree, params, dirs, n_rays, out, stream):
@@ -237,23 +245,29 @@ class Octree:
             pass
 
 
-class TraceParams:
-    """Host-side cone table for mt_trace_params."""
+INTERP = {"cic": MT_INTERP_CIC, "ngp": MT_INTERP_NGP, "tsc": MT_INTERP_TSC}
 
-    def __init__(self, observer, z_max, ray_begin, steps_per_cell=4, gravity_on=True, max_steps=1 << 22):
+
+class TraceParams:
+    """Host-side cone table for mt_trace_params.  interp: "cic", "ngp" or "tsc" (or MT_INTERP_*)."""
+
+    def __init__(self, observer, z_max, ray_begin, steps_per_cell=4, gravity_on=True, max_steps=1 << 22,
+                 interp="cic"):
         self.obs = np.ascontiguousarray(np.asarray(observer, dtype=np.float64).reshape(-1, 3))
         self.zmax = np.ascontiguousarray(np.atleast_1d(np.asarray(z_max, dtype=np.float64)))
         self.begin = np.ascontiguousarray(np.asarray(ray_begin, dtype=np.int64))
-        self.c = mt_trace_params(int(self.obs.shape[0]), int(steps_per_cell), 1 if gravity_on else 0, 0,
+        self.interp = INTERP[interp] if isinstance(interp, str) else int(interp)
+        self.c = mt_trace_params(int(self.obs.shape[0]), int(steps_per_cell), 1 if gravity_on else 0, self.interp,
                                  self.obs.ctypes.data_as(ctypes.c_void_p), self.zmax.ctypes.data_as(ctypes.c_void_p),
                                  self.begin.ctypes.data_as(ctypes.c_void_p), int(max_steps))
 
     @classmethod
-    def from_workload(cls, w, gravity_on=True, max_steps=None, steps_per_cell=None, ray_begin=None):
+    def from_workload(cls, w, gravity_on=True, max_steps=None, steps_per_cell=None, ray_begin=None, interp="cic"):
         spc = w.steps_per_cell if steps_per_cell is None else steps_per_cell
         if max_steps is None:
             max_steps = step_cap(w.bg, w.box / w.n_coarse, len(w.levels) - 1, spc, float(np.max(w.z_max)))
-        return cls(w.observer, w.z_max, w.ray_begin if ray_begin is None else ray_begin, spc, gravity_on, max_steps)
+        return cls(w.observer, w.z_max, w.ray_begin if ray_begin is None else ray_begin, spc, gravity_on, max_steps,
+                   interp)
 
 
 def step_cap(bg, dx0, n_levels, steps_per_cell, z_max):
@@ -333,6 +347,26 @@ def trace_rays_adjoint(tree: Octree, params: TraceParams, dirs, jacobian=True, l
         res["lens"] = lens
     if dL_dxi is not None:
         res["dL_drec"] = dL_drec
+    return res
+
+
+def trace_rays_lensing(tree: Octree, params: TraceParams, dirs, out=None, stream=None):
+    """mt_trace_rays_lensing on CUDA tensors: the ray outputs plus the infinitesimal-beam
+    distortion matrix "jac" [4, N] and "lens" [5, N] (Eq. 12; Born approximation when the
+    parameters have gravity off)."""
+    torch = _require_cuda()
+    n = int(dirs.shape[1])
+    if out is None:
+        out = alloc_outputs(n, dirs.device)
+    jac = torch.empty((4, n), dtype=torch.float64, device=dirs.device)
+    lens = torch.empty((5, n), dtype=torch.float64, device=dirs.device)
+    o = ray_out_struct(out)
+    _check(load().mt_trace_rays_lensing(tree.handle, ctypes.byref(params.c), dirs.data_ptr(), n, ctypes.byref(o),
+                                        jac.data_ptr(), lens.data_ptr(), _stream_handle(stream)),
+           "mt_trace_rays_lensing")
+    res = dict(out)
+    res["jac"] = jac
+    res["lens"] = lens
     return res
 
 

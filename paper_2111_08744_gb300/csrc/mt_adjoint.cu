@@ -333,7 +333,7 @@ cudaError_t launch_adjoint(const mt_octree* tree, const DevCones& C, const doubl
                            const TraceArgs& A, const double* dL_dxi, const RecBar& R, int seg_len, int* d_steps,
                            long long** d_off_out, double** d_ck_out, cudaStream_t stream) {
   const long long n = A.n_rays;
-  count_steps_kernel<T><<<(int)std::min<long long>((n + 127) / 128, 65535), 128, 0, stream>>>(tree->f, C, dirs, A,
+  count_steps_kernel<T><<<(int)std::min<long long>((n + 127) / 128, 65535), 128, 0, stream>>>(launch_field(tree, A), C, dirs, A,
                                                                                             d_steps, tree->ws);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -355,7 +355,7 @@ cudaError_t launch_adjoint(const mt_octree* tree, const DevCones& C, const doubl
   int bps = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, adjoint_kernel<T>, kAdjBlock, 0);
   if (bps < 1) bps = 1;
-  adjoint_kernel<T><<<tree->num_sms * bps, kAdjBlock, 0, stream>>>(tree->f, C, dirs, O, A, dL_dxi, R, *d_ck_out,
+  adjoint_kernel<T><<<tree->num_sms * bps, kAdjBlock, 0, stream>>>(launch_field(tree, A), C, dirs, O, A, dL_dxi, R, *d_ck_out,
                                                                     *d_off_out, seg_len, tree->ws);
   return cudaGetLastError();
 }
@@ -402,6 +402,7 @@ extern "C" mt_status mt_trace_rays_adjoint(const mt_octree* tree, const mt_trace
   if (!fwd && !rev) return MT_ERR_INVALID_ARG;
   if (rev && (!dL_dxi || !dL_drec)) return MT_ERR_INVALID_ARG;
   if (rev && (checkpoint_every < 1 || checkpoint_every > 64)) return MT_ERR_INVALID_ARG;
+  if (rev && params->interp != MT_INTERP_CIC) return MT_ERR_UNSUPPORTED;
   if (n_rays > 0 && !dirs) return MT_ERR_INVALID_ARG;
   if (n_rays == 0) return MT_OK;
   int prev = -1;
@@ -414,6 +415,8 @@ extern "C" mt_status mt_trace_rays_adjoint(const mt_octree* tree, const mt_trace
                out->d_a, out->d_l, out->phi_o, out->phi_s, out->isw, out->n_steps, out->level, out->status, out->xi};
   TraceArgs A;
   A.steps_per_cell = params->steps_per_cell;
+  A.interp = params->interp;
+  A.pad = 0;
   A.gravity_on = params->gravity_on ? 1 : 0;
   A.max_steps = params->max_steps;
   A.n_rays = n_rays;

@@ -34,7 +34,7 @@ struct FieldD {
 
 // CIC with level fallback (as sample_field) that also returns the spatial derivatives of the
 // trilinear interpolant.
-template <class T>
+template <class T, int IP = MT_INTERP_CIC>
 __device__ __forceinline__ bool sample_field_d(const DevField& F, const double* x, double eta, FieldD* fd, int* lf, unsigned* err) {
   using V = typename Vec4<T>::type;
   double u[3];
@@ -46,8 +46,28 @@ __device__ __forceinline__ bool sample_field_d(const DevField& F, const double* 
   const int s1 = F.S > 1 ? s + 1 : s;
   double v[8], dv[3][8];
   int l = lfin;
+  const int ip = IP >= 0 ? IP : F.interp;
   for (; l >= 0; --l) {
     const double sc = (double)(1ll << l);
+    if (ip != MT_INTERP_CIC) {  // NGP (piecewise constant: zero spatial derivative) or TSC
+      long long c[3];
+      double t[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const double U = u[d] * sc;
+        const double fl = floor(U);
+        c[d] = (long long)fl;
+        t[d] = U - fl - 0.5;
+      }
+      if (ip == MT_INTERP_NGP) {
+        if (!ngp_gather<T, double>(F, l, c, s, v, err)) continue;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dv[0][q] = dv[1][q] = dv[2][q] = 0.0;
+      } else if (!tsc_gather<T, double>(F, l, c, t, s, v, err, dv)) {
+        continue;
+      }
+      break;
+    }
     long long i0[3];
     double f[3];
 #pragma unroll

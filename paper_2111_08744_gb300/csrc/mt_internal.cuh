@@ -51,7 +51,7 @@ struct DevField {
   double seta[kMaxSlices];
   const dvec4* bg;  // (eta, a, H, dH/deta) nodes, uniform in eta
   int bg_n;
-  int pad;
+  int interp;       // MT_INTERP_CIC / NGP / TSC (set per launch from the trace parameters)
   double bg_eta0, bg_deta, bg_inv_deta;
   double eta_o;     // observer time = last background node
   // mixed-precision path: finest-level integer coordinates and single-precision tables
@@ -285,12 +285,184 @@ __device__ __forceinline__ bool cic_level(const DevField& F, int l, const double
   return cic_gather<T>(F, l, i0, f, s, out, err);
 }
 
+// ----------------------------------------------------------------- NGP and TSC (Eqs. 7, 9)
+
+// The parent octets of the 3 x 3 x 3 cells around cell c of level l >= 1: along each axis
+// the three cells c-1, c, c+1 have exactly two distinct parents, so 8 probes cover the 27
+// cells.  a[d][m] receives the wrapped coordinate of cell c + m - 1, oct[q] the octet of
+// parent (q & 1, q >> 1 & 1, q >> 2) (lower or upper parent per axis).  False when one of the
+// cells is outside a non-periodic domain or its octet is absent.
+__device__ __forceinline__ bool tsc_octets(const DevField& F, int l, const long long* c, unsigned (*a)[3],
+                                           unsigned* plo, unsigned* oct, unsigned* err) {
+  const long long Nl = (long long)F.nc << l;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      long long v = c[d] + m - 1;
+      if (F.periodic) {
+        v &= (Nl - 1);
+      } else if (v < 0 || v >= Nl) {
+        return false;
+      }
+      a[d][m] = (unsigned)v;
+    }
+    plo[d] = a[d][0] >> 1;
+  }
+  if (l == 0) return true;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const unsigned px = (q & 1) ? a[0][2] >> 1 : plo[0];
+    const unsigned py = (q & 2) ? a[1][2] >> 1 : plo[1];
+    const unsigned pz = (q & 4) ? a[2][2] >> 1 : plo[2];
+    const long long o = hash_find(F.hash[l], morton(px, py, pz), err);
+    if (o < 0) return false;
+    oct[q] = (unsigned)o;
+  }
+  return true;
+}
+
+// Row of cell (mx, my, mz) in {0,1,2}^3 of the neighbourhood described by tsc_octets.
+__device__ __forceinline__ unsigned tsc_row(int l, const unsigned (*a)[3], const unsigned* plo, const unsigned* oct,
+                                            int mx, int my, int mz) {
+  const unsigned x = a[0][mx], y = a[1][my], z = a[2][mz];
+  if (l == 0) return (unsigned)morton(x, y, z);
+  const int q = ((x >> 1) != plo[0] ? 1 : 0) | ((y >> 1) != plo[1] ? 2 : 0) | ((z >> 1) != plo[2] ? 4 : 0);
+  return oct[q] * 8u + ((x & 1u) | ((y & 1u) << 1) | ((z & 1u) << 2));
+}
+
+// TSC weights of Eq. (9) for the cells c-1, c, c+1 along one axis, t = U - c - 1/2 in [-1/2, 1/2)
+// (distances 1 + t, t, 1 - t from their centres); dw: derivatives with respect to U.
+template <class T>
+__device__ __forceinline__ void tsc_weights(T t, T* w, T* dw) {
+  const T lo = (T)0.5 - t, hi = (T)0.5 + t;
+  w[0] = (T)0.5 * lo * lo;
+  w[1] = (T)0.75 - t * t;
+  w[2] = (T)0.5 * hi * hi;
+  if (dw) {
+    dw[0] = -lo;
+    dw[1] = (T)-2 * t;
+    dw[2] = hi;
+  }
+}
+
+// TSC gather at level l around cell c (t as in tsc_weights), slices s, s+1 as cic_gather; with
+// dout, dout[d][q] receives the derivative with respect to the level-l coordinate d.  R: record
+// precision, T: arithmetic.
+template <class R, class T = R>
+__device__ __forceinline__ bool tsc_gather(const DevField& F, int l, const long long* c, const T* t, int s, T* out,
+                                          unsigned* err, T (*dout)[8] = nullptr) {
+  using V = typename Vec4<R>::type;
+  unsigned a[3][3], plo[3], oct[8];
+  if (!tsc_octets(F, l, c, a, plo, oct, err)) return false;
+  T w[3][3], dw[3][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) tsc_weights<T>(t[d], w[d], dout ? dw[d] : nullptr);
+  const V* rec = (const V*)F.rec[l];
+  const int S = F.S;
+  const int s1 = (S > 1) ? s + 1 : s;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) out[q] = (T)0;
+  if (dout) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) dout[0][q] = dout[1][q] = dout[2][q] = (T)0;
+  }
+#pragma unroll 1
+  for (int mz = 0; mz < 3; ++mz) {
+#pragma unroll 1
+    for (int my = 0; my < 3; ++my) {
+#pragma unroll
+      for (int mx = 0; mx < 3; ++mx) {
+        const V* rc = rec + (size_t)tsc_row(l, a, plo, oct, mx, my, mz) * (size_t)S;
+        const V r0 = ldg4(rc + s), r1 = ldg4(rc + s1);
+        const T rr[8] = {(T)r0.x, (T)r0.y, (T)r0.z, (T)r0.w, (T)r1.x, (T)r1.y, (T)r1.z, (T)r1.w};
+        const T wyz = w[1][my] * w[2][mz];
+        const T wgt = w[0][mx] * wyz;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) out[q] += wgt * rr[q];
+        if (dout) {
+          const T d0 = dw[0][mx] * wyz, d1 = w[0][mx] * dw[1][my] * w[2][mz], d2 = w[0][mx] * w[1][my] * dw[2][mz];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            dout[0][q] += d0 * rr[q];
+            dout[1][q] += d1 * rr[q];
+            dout[2][q] += d2 * rr[q];
+          }
+        }
+      }
+    }
+  }
+  return true;
+}
+
+// NGP (Eq. 7): the records of cell c of level l (slices s, s+1 as cic_gather).
+template <class R, class T = R>
+__device__ __forceinline__ bool ngp_gather(const DevField& F, int l, const long long* c, int s, T* out, unsigned* err) {
+  using V = typename Vec4<R>::type;
+  const long long Nl = (long long)F.nc << l;
+  unsigned v[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    long long x = c[d];
+    if (F.periodic) {
+      x &= (Nl - 1);
+    } else if (x < 0 || x >= Nl) {
+      return false;
+    }
+    v[d] = (unsigned)x;
+  }
+  unsigned long long row;
+  if (l == 0) {
+    row = morton(v[0], v[1], v[2]);
+  } else {
+    const long long o = hash_find(F.hash[l], morton(v[0] >> 1, v[1] >> 1, v[2] >> 1), err);
+    if (o < 0) return false;
+    row = (unsigned long long)o * 8ull + ((v[0] & 1u) | ((v[1] & 1u) << 1) | ((v[2] & 1u) << 2));
+  }
+  const V* rc = (const V*)F.rec[l] + (size_t)row * (size_t)F.S;
+  const V r0 = ldg4(rc + s), r1 = ldg4(rc + ((F.S > 1) ? s + 1 : s));
+  out[0] = (T)r0.x;
+  out[1] = (T)r0.y;
+  out[2] = (T)r0.z;
+  out[3] = (T)r0.w;
+  out[4] = (T)r1.x;
+  out[5] = (T)r1.y;
+  out[6] = (T)r1.z;
+  out[7] = (T)r1.w;
+  return true;
+}
+
+// Interpolation scheme of a code path: MT_INTERP_* fixed at compile time (the per-step code of
+// the kernels is instantiated per scheme, so CIC carries no TSC registers), or kInterpRuntime to
+// read DevField::interp (the once-per-ray observer and end-point samples).
+constexpr int kInterpRuntime = -1;
+
+// The interpolation scheme at level l from coarse-cell coordinates u.
+template <class T, int IP = MT_INTERP_CIC>
+__device__ __forceinline__ bool interp_level(const DevField& F, int l, const double* u, int s, T* out, unsigned* err) {
+  const int ip = IP >= 0 ? IP : F.interp;
+  if (ip == MT_INTERP_CIC) return cic_level<T>(F, l, u, s, out, err);
+  const double sc = (double)(1ll << l);
+  long long c[3];
+  T t[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double U = u[d] * sc;
+    const double fl = floor(U);
+    c[d] = (long long)fl;
+    t[d] = (T)(U - fl - 0.5);
+  }
+  if (ip == MT_INTERP_NGP) return ngp_gather<T>(F, l, c, s, out, err);
+  return tsc_gather<T>(F, l, c, t, s, out, err);
+}
+
 // Field at (x, eta): phi, grad phi and d phi/d eta, with the level fallback of Sect. 2.2
-// (start at the most refined level containing the photon; while one of the 8 CIC
-// neighbours is missing, retry one level coarser).  Time: linear in eta between the
+// (start at the most refined level containing the photon; while one of the cells the scheme
+// needs -- 8 for CIC, 27 for TSC -- is missing, retry one level coarser; NGP takes the
+// containing cell).  Time: linear in eta between the
 // bracketing slices, extended linearly outside them.  *lf receives the most refined
 // level.  Returns false when the point is outside a non-periodic domain.
-template <class T>
+template <class T, int IP = MT_INTERP_CIC>
 __device__ __forceinline__ bool sample_field(const DevField& F, const double* x, double eta, T* phi, T* g, T* pe,
                                              int* lf, unsigned* err) {
   double u[3];
@@ -302,7 +474,7 @@ __device__ __forceinline__ bool sample_field(const DevField& F, const double* x,
   T v[8];
   int l = lfin;
   for (; l >= 0; --l)
-    if (cic_level<T>(F, l, u, s, v, err)) break;
+    if (interp_level<T, IP>(F, l, u, s, v, err)) break;
   if (l < 0) return false;
   if (F.S == 1) {
     *phi = v[0];

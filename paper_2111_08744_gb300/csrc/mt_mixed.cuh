@@ -66,11 +66,17 @@ struct LaneCache {
   float4* rec;   // rec[j * stride] for j = 0..15 (corner-major, lanes interleaved: no bank conflicts)
   int4* key;     // (level << 8 | slice, i0x, i0y, i0z); level -1: empty
   int stride;
+  int* loc;      // last coarse cell looked up, packed x | y << 10 | z << 20, bit 30: refined; -1: empty
+                 // (a property of the field, valid across rays; used when N_0 <= 1024; may be null)
 };
 
-// CIC at level l (FP32) from finest-level integer coordinates; v as in cic_gather.
+// CIC at level l (FP32) from finest-level integer coordinates; v as in cic_gather.  With
+// WithD, dv[d][q] also receives the derivative of the interpolant of component q with respect
+// to the level-l cell coordinate d (the weights' derivatives, +-1 times the other two weights).
+template <bool WithD = false>
 __device__ __forceinline__ bool cic_int_cached(const DevField& F, int l, const int* ic, const float* fc, int s,
-                                               float* v, unsigned* err, const LaneCache& lc) {
+                                               float* v, unsigned* err, const LaneCache& lc,
+                                               float (*dv)[8] = nullptr) {
   const int sh = F.L - l;
   const float inv = 1.0f / (float)(1 << sh);
   int i0[3];
@@ -107,6 +113,10 @@ __device__ __forceinline__ bool cic_int_cached(const DevField& F, int l, const i
   }
 #pragma unroll
   for (int q = 0; q < 8; ++q) v[q] = 0.0f;
+  if constexpr (WithD) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) dv[0][q] = dv[1][q] = dv[2][q] = 0.0f;
+  }
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const float wx = (c & 1) ? f[0] : 1.0f - f[0];
@@ -123,6 +133,15 @@ __device__ __forceinline__ bool cic_int_cached(const DevField& F, int l, const i
     v[5] += w * r1.y;
     v[6] += w * r1.z;
     v[7] += w * r1.w;
+    if constexpr (WithD) {
+      const float dw[3] = {((c & 1) ? 1.0f : -1.0f) * wy * wz, ((c & 2) ? 1.0f : -1.0f) * wx * wz,
+                           ((c & 4) ? 1.0f : -1.0f) * wx * wy};
+      const float rr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dv[d][q] += dw[d] * rr[q];
+    }
   }
   return true;
 }
@@ -149,13 +168,55 @@ __device__ __forceinline__ bool cic_int(const DevField& F, int l, const int* ic,
   return cic_gather<float>(F, l, i0, f, s, v, err);
 }
 
+// NGP or TSC (Eqs. 7, 9) at level l (FP32) from finest-level integer coordinates: the level-l
+// cell is ic >> (L - l) and t the position in it relative to its centre; v (and dv with WithD)
+// as in cic_int_cached.  No lane cache: the 27 TSC cells are gathered every stage.
+template <bool WithD, int IP>
+__device__ __forceinline__ bool interp_int(const DevField& F, int l, const int* ic, const float* fc, int s, float* v,
+                                           unsigned* err, float (*dv)[8] = nullptr) {
+  const int sh = F.L - l;
+  const float inv = 1.0f / (float)(1 << sh);
+  long long c[3];
+  float t[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    c[d] = ic[d] >> sh;
+    t[d] = ((float)(ic[d] & ((1 << sh) - 1)) + fc[d]) * inv - 0.5f;
+  }
+  if constexpr (IP == MT_INTERP_NGP) {
+    if constexpr (WithD) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) dv[0][q] = dv[1][q] = dv[2][q] = 0.0f;
+    }
+    return ngp_gather<float>(F, l, c, s, v, err);
+  }
+  return tsc_gather<float>(F, l, c, t, s, v, err, WithD ? dv : nullptr);
+}
+
 // Most refined level containing the finest cell ic: the coarse refinement bitmap answers
 // level 1 (a 4-byte load from a small, cache-resident array), hash probes the deeper levels.
-__device__ __forceinline__ int locate_level_int(const DevField& F, const int* ic, unsigned* err) {
+__device__ __forceinline__ int locate_level_int(const DevField& F, const int* ic, unsigned* err,
+                                                const LaneCache* lc = nullptr) {
   if (F.L == 0) return 0;
   const unsigned sh0 = (unsigned)F.L;
-  const unsigned long long crow = morton((unsigned)ic[0] >> sh0, (unsigned)ic[1] >> sh0, (unsigned)ic[2] >> sh0);
-  if (!((__ldg(&F.refbits[crow >> 5]) >> (crow & 31ull)) & 1u)) return 0;
+  const unsigned cx = (unsigned)ic[0] >> sh0, cy = (unsigned)ic[1] >> sh0, cz = (unsigned)ic[2] >> sh0;
+  if (lc && lc->loc && F.nc <= 1024) {
+    // consecutive stages of a ray nearly always stay in one coarse cell: reuse its refinement bit
+    const int packed = (int)(cx | (cy << 10) | (cz << 20));
+    const int old = *lc->loc;
+    bool refined;
+    if (old >= 0 && (old & 0x3fffffff) == packed) {
+      refined = (old >> 30) != 0;
+    } else {
+      const unsigned long long crow = morton(cx, cy, cz);
+      refined = ((__ldg(&F.refbits[crow >> 5]) >> (crow & 31ull)) & 1u) != 0;
+      *lc->loc = packed | (refined ? (1 << 30) : 0);
+    }
+    if (!refined) return 0;
+  } else {
+    const unsigned long long crow = morton(cx, cy, cz);
+    if (!((__ldg(&F.refbits[crow >> 5]) >> (crow & 31ull)) & 1u)) return 0;
+  }
   int lf = 1;
   for (int l = 2; l <= F.L; ++l) {
     const int sh = F.L - l + 1;
@@ -176,12 +237,23 @@ struct MixedStep {
   float e_hi;    // eta_step - eta_{sb+1}
 };
 
+// What the tangent of the right-hand side needs at a stage (FP32): the interpolated force and
+// phi_eta, D = d phi / d lambda of Eq. (4), H, and their derivatives.
+struct StageF {
+  float g[3], pe, D, H, dH;
+  float G[3][3];  // G[i][d] = d g_i / d x_d (derivative of the trilinear interpolant)
+  float ge[3];    // d g_i / d eta (slope between the bracketing slices)
+  float dpe[3];   // d phi_eta / d x_d
+};
+
 // FP32 right-hand side of Eqs. (2)-(4) at the stage with offsets (offx, offe) from the step
-// start and wave vector (k0, k).  *lf (if non-null) receives the most refined level.
+// start and wave vector (k0, k).  *lf (if non-null) receives the most refined level.  With
+// WithD (which needs the lane cache) *sf receives the stage's field values and derivatives.
+template <bool WithD = false, int IP = MT_INTERP_CIC>
 __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const MixedStep& B, double eta_step,
                                           const float* offx, float offe, float k0, const float* k, float* Kk0,
                                           float* Kk, float* KI, float* Ks, int* lf, unsigned* err,
-                                          const LaneCache* lc) {
+                                          const LaneCache* lc, StageF* sf = nullptr) {
   // background H(eta_step + offe)
   const float t = B.tb + offe * F.bg_inv_deta_f;
   const float ct = floorf(t);
@@ -199,11 +271,23 @@ __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const Mi
   const float H = (2.0f * t3 - 3.0f * t2 + 1.0f) * p.x + (t3 - 2.0f * t2 + ft) * p.y + (-2.0f * t3 + 3.0f * t2) * p.z +
                   (t3 - t2) * p.w;
   float phi = 0.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, pe = 0.0f;
+  if constexpr (WithD) {
+    sf->H = H;
+    sf->dH = ((6.0f * t2 - 6.0f * ft) * p.x + (3.0f * t2 - 4.0f * ft + 1.0f) * p.y + (6.0f * ft - 6.0f * t2) * p.z +
+              (3.0f * t2 - 2.0f * ft) * p.w) *
+             F.bg_inv_deta_f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      sf->ge[i] = sf->dpe[i] = 0.0f;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) sf->G[i][d] = 0.0f;
+    }
+  }
   if (grav || lf) {
     int ic[3];
     float fc[3];
     if (!stage_coords(F, B.ib, B.fb, offx, ic, fc)) return false;
-    const int lfin = locate_level_int(F, ic, err);
+    const int lfin = locate_level_int(F, ic, err, lc);
     if (lf) *lf = lfin;
     if (grav) {
       int s = B.sb;
@@ -219,8 +303,15 @@ __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const Mi
         }
       }
       float v[8];
+      float dv[WithD ? 3 : 1][8];
       int l = lfin;
-      if (lc) {
+      if constexpr (IP != MT_INTERP_CIC) {
+        for (; l >= 0; --l)
+          if (interp_int<WithD, IP>(F, l, ic, fc, s, v, err, WithD ? dv : nullptr)) break;
+      } else if constexpr (WithD) {
+        for (; l >= 0; --l)
+          if (cic_int_cached<true>(F, l, ic, fc, s, v, err, *lc, dv)) break;
+      } else if (lc) {
         for (; l >= 0; --l)
           if (cic_int_cached(F, l, ic, fc, s, v, err, *lc)) break;
       } else {
@@ -242,10 +333,36 @@ __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const Mi
         g2 = v[3] + w * (v[7] - v[3]);
         pe = (v[4] - v[0]) * ids;
       }
+      if constexpr (WithD) {
+        const float inv = F.inv_dxf_f / (float)(1 << (F.L - l));  // d (level-l cell coordinate) / d x
+        if (F.S == 1) {
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) sf->G[i][d] = dv[d][1 + i] * inv;
+        } else {
+          const float ids = F.inv_dseta[s];
+          const float w = (es + offe) * ids;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            sf->ge[i] = (v[5 + i] - v[1 + i]) * ids;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) sf->G[i][d] = (dv[d][1 + i] + w * (dv[d][5 + i] - dv[d][1 + i])) * inv;
+            sf->dpe[i] = (dv[i][4] - dv[i][0]) * ids * inv;
+          }
+        }
+      }
     }
   }
   (void)phi;
   const float dphidl = g0 * k[0] + g1 * k[1] + g2 * k[2] + pe * k0;
+  if constexpr (WithD) {
+    sf->g[0] = g0;
+    sf->g[1] = g1;
+    sf->g[2] = g2;
+    sf->pe = pe;
+    sf->D = dphidl;
+  }
   const float k00 = k0 * k0;
   const float bg = -2.0f * H * k0;
   *Kk0 = bg * k0 - 2.0f * dphidl * k0 + 2.0f * pe * k00;
@@ -257,8 +374,25 @@ __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const Mi
   return true;
 }
 
+// Step-start quantities of a mixed step: finest-level base cell and fraction, background node
+// and slice bracket of eta.  False when the position is outside a non-periodic domain.
+__device__ __forceinline__ bool mixed_begin(const DevField& F, const double* y, MixedStep& B) {
+  if (!finest_base(F, y, B.ib, B.fb)) return false;
+  const double eta = y[3];
+  const double t0 = (eta - F.bg_eta0) * F.bg_inv_deta;
+  const double jf = floor(t0);
+  B.jb = (int)jf;
+  B.tb = (float)(t0 - jf);
+  int s = 0;
+  while (s < F.S - 2 && F.seta[s + 1] <= eta) ++s;
+  B.sb = s;
+  B.e_lo = (float)(eta - F.seta[s]);
+  B.e_hi = F.S > 1 ? (float)(eta - F.seta[s + 1]) : 0.0f;
+  return true;
+}
+
 // One mixed-precision RK4 step; state and status conventions as ray_step.
-template <class RayStateT, class TraceArgsT>
+template <int IP = MT_INTERP_CIC, class RayStateT, class TraceArgsT>
 __device__ bool ray_step_mixed(const DevField& F, const TraceArgsT& A, RayStateT& r, unsigned* err,
                                const LaneCache* lc = nullptr) {
   if (r.n_steps == 0 && !(r.y[3] > r.eta_stop)) return true;
@@ -268,22 +402,11 @@ __device__ bool ray_step_mixed(const DevField& F, const TraceArgsT& A, RayStateT
   }
   const bool grav = A.gravity_on != 0;
   MixedStep B;
-  if (!finest_base(F, r.y, B.ib, B.fb)) {
+  if (!mixed_begin(F, r.y, B)) {
     r.status = MT_RAY_LEFT_DOMAIN;
     return true;
   }
   const double eta = r.y[3];
-  {
-    const double t0 = (eta - F.bg_eta0) * F.bg_inv_deta;
-    const double jf = floor(t0);
-    B.jb = (int)jf;
-    B.tb = (float)(t0 - jf);
-    int s = 0;
-    while (s < F.S - 2 && F.seta[s + 1] <= eta) ++s;
-    B.sb = s;
-    B.e_lo = (float)(eta - F.seta[s]);
-    B.e_hi = F.S > 1 ? (float)(eta - F.seta[s + 1]) : 0.0f;
-  }
   const float k0s = (float)r.y[4];
   const float ks[3] = {(float)r.y[5], (float)r.y[6], (float)r.y[7]};
   // stage offsets (from the step start) and weighted sums of the stage derivatives
@@ -297,7 +420,8 @@ __device__ bool ray_step_mixed(const DevField& F, const TraceArgsT& A, RayStateT
     const float kst[3] = {ks[0] + offk[0], ks[1] + offk[1], ks[2] + offk[2]};
     float Kk0, Kk[3], KI, Ks;
     int lf = 0;
-    if (!rhs_mixed(F, grav, B, eta, offx, offe, kst0, kst, &Kk0, Kk, &KI, &Ks, st == 0 ? &lf : nullptr, err, lc)) {
+    if (!rhs_mixed<false, IP>(F, grav, B, eta, offx, offe, kst0, kst, &Kk0, Kk, &KI, &Ks, st == 0 ? &lf : nullptr, err,
+                              lc)) {
       r.status = MT_RAY_LEFT_DOMAIN;
       return true;
     }

@@ -25,7 +25,7 @@ constexpr int kTanBlock = 128;
 
 // Right-hand side K = f(y) (as geodesic_rhs) and its tangents dK_b = J(y) dY_b, b = 0, 1.
 // Tangent layout: dx[3], deta, dk0, dk[3].
-template <class T>
+template <class T, int IP>
 __device__ bool rhs_tangent(const DevField& F, bool grav, const double* y, const double (*dY)[8], double* K,
                             double (*dK)[8], int* lf, unsigned* err) {
   double H, dH;
@@ -34,7 +34,7 @@ __device__ bool rhs_tangent(const DevField& F, bool grav, const double* y, const
   FieldD fd = {};
   if (grav) {
     int l;
-    if (!sample_field_d<T>(F, y, y[3], &fd, &l, err)) return false;
+    if (!sample_field_d<T, IP>(F, y, y[3], &fd, &l, err)) return false;
     if (lf) *lf = l;
   } else if (lf) {
     double u[3];
@@ -81,7 +81,7 @@ struct TanState {
 };
 
 // One RK4 step of the state and its two tangents.  Returns true when the ray is finished.
-template <class T>
+template <class T, int IP>
 __device__ bool tangent_step(const DevField& F, const TraceArgs& A, RayState& r, TanState& ts, unsigned* err) {
   if (r.n_steps == 0 && !(r.y[3] > r.eta_stop)) return true;
   if (r.n_steps >= A.max_steps) {
@@ -92,7 +92,7 @@ __device__ bool tangent_step(const DevField& F, const TraceArgs& A, RayState& r,
   double K[10], acc[10], t[10];
   double dK[2][8], dacc[2][8], dt[2][8];
   int lf = 0;
-  if (!rhs_tangent<T>(F, grav, r.y, ts.d, K, dK, &lf, err)) {
+  if (!rhs_tangent<T, IP>(F, grav, r.y, ts.d, K, dK, &lf, err)) {
     r.status = MT_RAY_LEFT_DOMAIN;
     return true;
   }
@@ -119,7 +119,7 @@ __device__ bool tangent_step(const DevField& F, const TraceArgs& A, RayState& r,
       dacc[b][i] = ts.d[b][i] + (dh[b] / 6.0) * K[i] + h6 * dK[b][i];
       dt[b][i] = ts.d[b][i] + (0.5 * dh[b]) * K[i] + h2 * dK[b][i];
     }
-  if (!rhs_tangent<T>(F, grav, t, dt, K, dK, nullptr, err)) {
+  if (!rhs_tangent<T, IP>(F, grav, t, dt, K, dK, nullptr, err)) {
     r.status = MT_RAY_LEFT_DOMAIN;
     return true;
   }
@@ -132,7 +132,7 @@ __device__ bool tangent_step(const DevField& F, const TraceArgs& A, RayState& r,
       dacc[b][i] += (dh[b] / 3.0) * K[i] + h3 * dK[b][i];
       dt[b][i] = ts.d[b][i] + (0.5 * dh[b]) * K[i] + h2 * dK[b][i];
     }
-  if (!rhs_tangent<T>(F, grav, t, dt, K, dK, nullptr, err)) {
+  if (!rhs_tangent<T, IP>(F, grav, t, dt, K, dK, nullptr, err)) {
     r.status = MT_RAY_LEFT_DOMAIN;
     return true;
   }
@@ -145,7 +145,7 @@ __device__ bool tangent_step(const DevField& F, const TraceArgs& A, RayState& r,
       dacc[b][i] += (dh[b] / 3.0) * K[i] + h3 * dK[b][i];
       dt[b][i] = ts.d[b][i] + dh[b] * K[i] + h * dK[b][i];
     }
-  if (!rhs_tangent<T>(F, grav, t, dt, K, dK, nullptr, err)) {
+  if (!rhs_tangent<T, IP>(F, grav, t, dt, K, dK, nullptr, err)) {
     r.status = MT_RAY_LEFT_DOMAIN;
     return true;
   }
@@ -157,6 +157,159 @@ __device__ bool tangent_step(const DevField& F, const TraceArgs& A, RayState& r,
   for (int b = 0; b < 2; ++b)
     for (int i = 0; i < 8; ++i) ts.d[b][i] = dacc[b][i] + (dh[b] / 6.0) * K[i] + h6 * dK[b][i];
   r.lambda += h;
+  r.n_steps += 1;
+  if (!finite) {
+    r.status = MT_RAY_NONFINITE;
+    return true;
+  }
+  return last;
+}
+
+// Mixed-precision form for FP32 fields, arranged as ray_step_mixed: the ray advances exactly as
+// in the mixed trace (FP32 stages, FP64 state); the tangents' stage derivatives are FP32 and the
+// tangent state FP64.  Stage j of tangent b is dY_b + doff_b with doff_b = c_j (dh K + h dK) of
+// the previous stage, and the step adds sum_j b_j (dh K_j + h dK_j), as in tangent_step; the
+// parts linear in the step-start state (dh k + h dk for the position-like components) are
+// applied in FP64, the stage corrections in FP32.
+template <int IP>
+__device__ bool tangent_step_mixed(const DevField& F, const TraceArgs& A, RayState& r, TanState& ts, unsigned* err,
+                                   const LaneCache* lc) {
+  if (r.n_steps == 0 && !(r.y[3] > r.eta_stop)) return true;
+  if (r.n_steps >= A.max_steps) {
+    r.status = MT_RAY_MAX_STEPS;
+    return true;
+  }
+  const bool grav = A.gravity_on != 0;
+  MixedStep B;
+  if (!mixed_begin(F, r.y, B)) {
+    r.status = MT_RAY_LEFT_DOMAIN;
+    return true;
+  }
+  const double eta = r.y[3];
+  const float k0s = (float)r.y[4];
+  const float ks[3] = {(float)r.y[5], (float)r.y[6], (float)r.y[7]};
+  float dst[2][8];
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) dst[b][i] = (float)ts.d[b][i];
+  float offx[3] = {0.0f, 0.0f, 0.0f}, offe = 0.0f, offk0 = 0.0f, offk[3] = {0.0f, 0.0f, 0.0f};
+  float sx[3] = {0.0f, 0.0f, 0.0f}, se = 0.0f, sk0 = 0.0f, sk[3] = {0.0f, 0.0f, 0.0f}, sI = 0.0f, ss = 0.0f;
+  float doff[2][8], sdo[2][4], sdK[2][4];
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) doff[b][i] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) sdo[b][i] = sdK[b][i] = 0.0f;
+  }
+  float h = 0.0f, dh[2] = {0.0f, 0.0f};
+  bool last = false;
+#pragma unroll 1
+  for (int st = 0; st < 4; ++st) {
+    const float kst0 = k0s + offk0;
+    const float kst[3] = {ks[0] + offk[0], ks[1] + offk[1], ks[2] + offk[2]};
+    float Kk0, Kk[3], KI, Ks;
+    StageF sf;
+    int lf = 0;
+    if (!rhs_mixed<true, IP>(F, grav, B, eta, offx, offe, kst0, kst, &Kk0, Kk, &KI, &Ks, st == 0 ? &lf : nullptr, err,
+                         lc, &sf)) {
+      r.status = MT_RAY_LEFT_DOMAIN;
+      return true;
+    }
+    if (st == 0) {
+      const float dxl = F.dx0_f / (float)(1 << lf);
+      h = dxl / ((float)A.steps_per_cell * fabsf(k0s));
+      const float d = (float)(r.eta_stop - eta);
+      if (k0s * h <= d) {
+        h = d / k0s;
+        last = true;
+      }
+#pragma unroll
+      for (int b = 0; b < 2; ++b) dh[b] = last ? -(dst[b][3] + h * dst[b][4]) / k0s : -h * dst[b][4] / k0s;
+    }
+    const float bw = (st == 0 || st == 3) ? (1.0f / 6.0f) : (1.0f / 3.0f);
+    const float a = st == 2 ? 1.0f : 0.5f;  // next stage at y + a h K, dY + a (dh K + h dK)
+    const float c = a * h;
+    const float k00 = kst0 * kst0;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      float t[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) t[i] = dst[b][i] + doff[b][i];
+      float dg[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) dg[i] = sf.G[i][0] * t[0] + sf.G[i][1] * t[1] + sf.G[i][2] * t[2] + sf.ge[i] * t[3];
+      const float dpe = sf.dpe[0] * t[0] + sf.dpe[1] * t[1] + sf.dpe[2] * t[2];
+      const float dHb = sf.dH * t[3];
+      const float dD = dg[0] * kst[0] + dg[1] * kst[1] + dg[2] * kst[2] + sf.g[0] * t[5] + sf.g[1] * t[6] +
+                       sf.g[2] * t[7] + dpe * kst0 + sf.pe * t[4];
+      float dK[4];
+      dK[0] = -2.0f * dHb * k00 - 4.0f * sf.H * kst0 * t[4] - 2.0f * dD * kst0 - 2.0f * sf.D * t[4] +
+              2.0f * dpe * k00 + 4.0f * sf.pe * kst0 * t[4];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        dK[1 + i] = -2.0f * dHb * kst0 * kst[i] - 2.0f * sf.H * t[4] * kst[i] - 2.0f * sf.H * kst0 * t[5 + i] +
+                    2.0f * dD * kst[i] + 2.0f * sf.D * t[5 + i] - 2.0f * dg[i] * k00 - 4.0f * sf.g[i] * kst0 * t[4];
+      sdo[b][0] += bw * doff[b][5];
+      sdo[b][1] += bw * doff[b][6];
+      sdo[b][2] += bw * doff[b][7];
+      sdo[b][3] += bw * doff[b][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) sdK[b][i] += bw * dK[i];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) doff[b][i] = a * (dh[b] * kst[i] + h * t[5 + i]);
+      doff[b][3] = a * (dh[b] * kst0 + h * t[4]);
+      doff[b][4] = a * (dh[b] * Kk0 + h * dK[0]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) doff[b][5 + i] = a * (dh[b] * Kk[i] + h * dK[1 + i]);
+    }
+    sk0 += bw * Kk0;
+    sk[0] += bw * Kk[0];
+    sk[1] += bw * Kk[1];
+    sk[2] += bw * Kk[2];
+    sI += bw * KI;
+    ss += bw * Ks;
+    se += bw * offk0;
+    sx[0] += bw * offk[0];
+    sx[1] += bw * offk[1];
+    sx[2] += bw * offk[2];
+    offx[0] = c * kst[0];
+    offx[1] = c * kst[1];
+    offx[2] = c * kst[2];
+    offe = c * kst0;
+    offk0 = c * Kk0;
+    offk[0] = c * Kk[0];
+    offk[1] = c * Kk[1];
+    offk[2] = c * Kk[2];
+  }
+  const double hd = (double)h;
+  // tangents first: their position-like parts use the step-start k and dk
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const double dhb = (double)dh[b];
+    double* d = ts.d[b];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[i] += dhb * r.y[5 + i] + hd * d[5 + i] + (double)(dh[b] * sx[i] + h * sdo[b][i]);
+    d[3] += dhb * r.y[4] + hd * d[4] + (double)(dh[b] * se + h * sdo[b][3]);
+    d[4] += (double)(dh[b] * sk0 + h * sdK[b][0]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[5 + i] += (double)(dh[b] * sk[i] + h * sdK[b][1 + i]);
+  }
+  bool finite = true;
+  r.y[0] += hd * r.y[5] + (double)(h * sx[0]);
+  r.y[1] += hd * r.y[6] + (double)(h * sx[1]);
+  r.y[2] += hd * r.y[7] + (double)(h * sx[2]);
+  r.y[3] += hd * r.y[4] + (double)(h * se);
+  r.y[4] += (double)(h * sk0);
+  r.y[5] += (double)(h * sk[0]);
+  r.y[6] += (double)(h * sk[1]);
+  r.y[7] += (double)(h * sk[2]);
+  r.y[8] += (double)(h * sI);
+  r.y[9] += (double)(h * ss);
+#pragma unroll
+  for (int i = 0; i < 10; ++i) finite = finite && isfinite(r.y[i]);
+  r.lambda += hd;
   r.n_steps += 1;
   if (!finite) {
     r.status = MT_RAY_NONFINITE;
@@ -199,30 +352,25 @@ __device__ __noinline__ void tangent_finish(const RayState r, const TanState ts,
   const double A12 = (dxi[1][0] * s1[0] + dxi[1][1] * s1[1] + dxi[1][2] * s1[2]) / chi;
   const double A21 = (dxi[0][0] * s2[0] + dxi[0][1] * s2[1] + dxi[0][2] * s2[2]) / chi;
   const double A22 = (dxi[1][0] * s2[0] + dxi[1][1] * s2[1] + dxi[1][2] * s2[2]) / chi;
-  if (jac) {
-    jac[ray] = A11;
-    jac[n + ray] = A12;
-    jac[2 * n + ray] = A21;
-    jac[3 * n + ray] = A22;
-  }
-  if (lens) {
-    // Eq. (11): A = R(omega) [[1 - kappa - gamma1, -gamma2], [-gamma2, 1 - kappa + gamma1]]
-    const double tr = A11 + A22, an = A21 - A12;
-    const double om = atan2(an, tr);
-    const double one_k = 0.5 * sqrt(tr * tr + an * an);
-    double so, co;
-    sincos(om, &so, &co);
-    const double S11 = co * A11 + so * A21, S12 = co * A12 + so * A22;
-    const double S21 = -so * A11 + co * A21, S22 = -so * A12 + co * A22;
-    lens[ray] = 1.0 - one_k;
-    lens[n + ray] = 0.5 * (S22 - S11);
-    lens[2 * n + ray] = -0.5 * (S12 + S21);
-    lens[3 * n + ray] = om;
-    lens[4 * n + ray] = A11 * A22 - A12 * A21;
+  write_distortion(A11, A12, A21, A22, ray, n, jac, lens);
+}
+
+// Initial tangents: the direction perturbed along the observer's screen vectors e_1, e_2.
+__device__ __noinline__ void tangent_init(const double* __restrict__ dirs, long long n, long long ray,
+                                          const RayState& r, TanState& ts) {
+  const double nd[3] = {__ldg(&dirs[ray]), __ldg(&dirs[n + ray]), __ldg(&dirs[2 * n + ray])};
+  double e1[3], e2[3];
+  screen_vectors(nd, e1, e2);
+  const double kn = sqrt(r.y[5] * r.y[5] + r.y[6] * r.y[6] + r.y[7] * r.y[7]) /
+                    sqrt(nd[0] * nd[0] + nd[1] * nd[1] + nd[2] * nd[2]);
+  for (int b = 0; b < 2; ++b) {
+    const double* e = b == 0 ? e1 : e2;
+    for (int i = 0; i < 5; ++i) ts.d[b][i] = 0.0;
+    for (int d = 0; d < 3; ++d) ts.d[b][5 + d] = kn * e[d];
   }
 }
 
-template <class T>
+template <class T, int IP>
 __global__ void __launch_bounds__(kTanBlock) tangent_kernel(DevField F, DevCones C, const double* __restrict__ dirs,
                                                             OutPtrs O, double* jac, double* lens, TraceArgs A,
                                                             unsigned long long* ws) {
@@ -249,17 +397,7 @@ __global__ void __launch_bounds__(kTanBlock) tangent_kernel(DevField F, DevCones
           int c = 0;
           while (c + 1 < C.n && C.begin[c + 1] <= ray) ++c;
           r = ray_start<T>(F, C.obs[c], C.eta_stop[c], dirs, n, ray, grav, err);
-          // initial tangents: direction perturbed along the observer's screen vectors e_1, e_2
-          const double nd[3] = {__ldg(&dirs[ray]), __ldg(&dirs[n + ray]), __ldg(&dirs[2 * n + ray])};
-          double e1[3], e2[3];
-          screen_vectors(nd, e1, e2);
-          const double kn = sqrt(r.y[5] * r.y[5] + r.y[6] * r.y[6] + r.y[7] * r.y[7]) /
-                            sqrt(nd[0] * nd[0] + nd[1] * nd[1] + nd[2] * nd[2]);
-          for (int b = 0; b < 2; ++b) {
-            const double* e = b == 0 ? e1 : e2;
-            for (int i = 0; i < 5; ++i) ts.d[b][i] = 0.0;
-            for (int d = 0; d < 3; ++d) ts.d[b][5 + d] = kn * e[d];
-          }
+          tangent_init(dirs, n, ray, r, ts);
         } else {
           exhausted = true;
         }
@@ -268,7 +406,7 @@ __global__ void __launch_bounds__(kTanBlock) tangent_kernel(DevField F, DevCones
     const bool alive = ray >= 0;
     if (!__any_sync(0xffffffffu, alive)) break;
     if (alive) {
-      if (tangent_step<T>(F, A, r, ts, err)) {
+      if (tangent_step<T, IP>(F, A, r, ts, err)) {
         ray_finish<T>(F, A, r, ray, n, O, err);
         tangent_finish(r, ts, ray, n, jac, lens);
         ray = -1;
@@ -277,16 +415,102 @@ __global__ void __launch_bounds__(kTanBlock) tangent_kernel(DevField F, DevCones
   }
 }
 
-template <class T>
-int tangent_blocks_per_sm() {
+// FP32 fields: the mixed tangent step, with each ray's CIC neighbourhood staged in shared
+// memory as in trace_kernel.
+template <int IP>
+__global__ void __launch_bounds__(kTanBlock) tangent_kernel_mixed(DevField F, DevCones C,
+                                                                  const double* __restrict__ dirs, OutPtrs O,
+                                                                  double* jac, double* lens, TraceArgs A,
+                                                                  unsigned long long* ws) {
+  unsigned* err = (unsigned*)(ws + 1);
+  const unsigned lane = threadIdx.x & 31u;
+  const long long n = A.n_rays;
+  const bool grav = A.gravity_on != 0;
+  extern __shared__ float4 smem[];
+  LaneCache lc;
+  lc.rec = smem + threadIdx.x;
+  lc.key = (int4*)(smem + 16 * kTanBlock) + threadIdx.x;
+  lc.stride = kTanBlock;
+  lc.loc = (int*)((int4*)(smem + 16 * kTanBlock) + kTanBlock) + threadIdx.x;
+  *lc.loc = -1;
+  RayState r;
+  TanState ts;
+  long long ray = -1;
+  bool exhausted = false;
+  for (;;) {
+    const bool need = (ray < 0) && !exhausted;
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(ws, (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (need) {
+        const long long id = (long long)base + __popc(m & ((1u << lane) - 1u));
+        if (id < n) {
+          ray = id;
+          int c = 0;
+          while (c + 1 < C.n && C.begin[c + 1] <= ray) ++c;
+          r = ray_start<float>(F, C.obs[c], C.eta_stop[c], dirs, n, ray, grav, err);
+          tangent_init(dirs, n, ray, r, ts);
+          *lc.key = make_int4(-1, 0, 0, 0);
+        } else {
+          exhausted = true;
+        }
+      }
+    }
+    const bool alive = ray >= 0;
+    if (!__any_sync(0xffffffffu, alive)) break;
+    if (alive) {
+      if (tangent_step_mixed<IP>(F, A, r, ts, err, &lc)) {
+        ray_finish<float>(F, A, r, ray, n, O, err);
+        tangent_finish(r, ts, ray, n, jac, lens);
+        ray = -1;
+      }
+    }
+  }
+}
+
+constexpr size_t kTanMixedSmem = (size_t)kTanBlock * (16 * sizeof(float4) + sizeof(int4) + sizeof(int));
+
+template <int IP>
+int tangent_mixed_blocks_per_sm() {
   static int cached = -1;
   if (cached < 0) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tangent_kernel<T>, kTanBlock, 0) != cudaSuccess || b < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tangent_kernel_mixed<IP>, kTanBlock, kTanMixedSmem) !=
+            cudaSuccess ||
+        b < 1)
       b = 1;
     cached = b;
   }
   return cached;
+}
+
+template <int IP>
+int tangent_blocks_per_sm() {
+  static int cached = -1;
+  if (cached < 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tangent_kernel<double, IP>, kTanBlock, 0) != cudaSuccess ||
+        b < 1)
+      b = 1;
+    cached = b;
+  }
+  return cached;
+}
+
+// FP64 field: FP64 tangent step; FP32 field: the mixed tangent step.
+template <int IP>
+void launch_tangent_scheme(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O,
+                           double* jac, double* lens, const TraceArgs& A, cudaStream_t stream) {
+  if (tree->precision == MT_FIELD_FP64) {
+    tangent_kernel<double, IP><<<tree->num_sms * tangent_blocks_per_sm<IP>(), kTanBlock, 0, stream>>>(
+        launch_field(tree, A), C, dirs, O, jac, lens, A, tree->ws);
+  } else {
+    tangent_kernel_mixed<IP><<<tree->num_sms * tangent_mixed_blocks_per_sm<IP>(), kTanBlock, kTanMixedSmem, stream>>>(
+        launch_field(tree, A), C, dirs, O, jac, lens, A, tree->ws);
+  }
 }
 
 }  // namespace
@@ -296,12 +520,10 @@ cudaError_t launch_tangent(const mt_octree* tree, const DevCones& C, const doubl
                            double* lens, const TraceArgs& A, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(tree->ws, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
-  if (tree->precision == MT_FIELD_FP64) {
-    tangent_kernel<double><<<tree->num_sms * tangent_blocks_per_sm<double>(), kTanBlock, 0, stream>>>(
-        tree->f, C, dirs, O, jac, lens, A, tree->ws);
-  } else {
-    tangent_kernel<float><<<tree->num_sms * tangent_blocks_per_sm<float>(), kTanBlock, 0, stream>>>(
-        tree->f, C, dirs, O, jac, lens, A, tree->ws);
+  switch (A.interp) {
+    case MT_INTERP_NGP: launch_tangent_scheme<MT_INTERP_NGP>(tree, C, dirs, O, jac, lens, A, stream); break;
+    case MT_INTERP_TSC: launch_tangent_scheme<MT_INTERP_TSC>(tree, C, dirs, O, jac, lens, A, stream); break;
+    default: launch_tangent_scheme<MT_INTERP_CIC>(tree, C, dirs, O, jac, lens, A, stream); break;
   }
   return cudaGetLastError();
 }

@@ -25,7 +25,8 @@ __device__ void ray_init(const DevField& F, const DevCones& C, const double* __r
 }
 
 // BS threads per block; the register budget (128 per thread) is the same for every block size.
-template <class T, int BS>
+// IP: the interpolation scheme (MT_INTERP_*), fixed per instantiation.
+template <class T, int BS, int IP>
 __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCones C, const double* __restrict__ dirs,
                                                               OutPtrs O, TraceArgs A, unsigned long long* ws) {
   unsigned* err = (unsigned*)(ws + 1);
@@ -38,6 +39,8 @@ __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCone
   lc.rec = smem + threadIdx.x;
   lc.key = (int4*)(smem + 16 * BS) + threadIdx.x;
   lc.stride = BS;
+  lc.loc = (int*)((int4*)(smem + 16 * BS) + BS) + threadIdx.x;
+  if (sizeof(T) == 4) *lc.loc = -1;
   const LaneCache* lcp = sizeof(T) == 4 ? &lc : nullptr;
   RayState r;
   long long ray = -1;
@@ -64,7 +67,7 @@ __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCone
     const bool alive = ray >= 0;
     if (!__any_sync(0xffffffffu, alive)) break;
     if (alive) {
-      if (ray_step<T>(F, A, r, err, lcp)) {
+      if (ray_step<T, IP>(F, A, r, err, lcp)) {
         ray_finish<T>(F, A, r, ray, n, O, err);
         ray = -1;
       }
@@ -75,39 +78,50 @@ __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCone
 // Dynamic shared memory of trace_kernel<T, BS>: the mixed path's per-thread neighbourhood cache.
 template <class T, int BS>
 constexpr size_t trace_smem() {
-  return sizeof(T) == 4 ? (size_t)BS * (16 * sizeof(float4) + sizeof(int4)) : 0;
+  return sizeof(T) == 4 ? (size_t)BS * (16 * sizeof(float4) + sizeof(int4) + sizeof(int)) : 0;
 }
 
-template <class T, int BS>
+template <class T, int BS, int IP>
 int blocks_per_sm() {
   static int cached = -1;
   if (cached < 0) {
     const size_t sm = trace_smem<T, BS>();
-    if (sm > 48 * 1024) cudaFuncSetAttribute(trace_kernel<T, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(trace_kernel<T, BS, IP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<T, BS>, BS, sm) != cudaSuccess || b < 1) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<T, BS, IP>, BS, sm) != cudaSuccess || b < 1)
+      b = 1;
     cached = b;
   }
   return cached;
 }
 
-template <class T, int BS>
+template <class T, int BS, int IP>
 void launch_trace_bs(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O,
                      const TraceArgs& A, cudaStream_t stream) {
-  int bps = blocks_per_sm<T, BS>();
+  int bps = blocks_per_sm<T, BS, IP>();
   if (tree->launch_bps > 0 && tree->launch_bps < bps) bps = tree->launch_bps;
-  trace_kernel<T, BS><<<tree->num_sms * bps, BS, trace_smem<T, BS>(), stream>>>(tree->f, C, dirs, O, A, tree->ws);
+  trace_kernel<T, BS, IP><<<tree->num_sms * bps, BS, trace_smem<T, BS>(), stream>>>(launch_field(tree, A), C, dirs,
+                                                                                    O, A, tree->ws);
 }
 
 // Launch shape: the octree's configuration (mt_set_launch_config), default 128 threads and as
-// many blocks per SM as fit.
+// many blocks per SM as fit.  NGP and TSC run with 128 threads per block.
 template <class T>
 void launch_trace(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O, const TraceArgs& A,
                   cudaStream_t stream) {
+  if (A.interp == MT_INTERP_NGP) {
+    launch_trace_bs<T, 128, MT_INTERP_NGP>(tree, C, dirs, O, A, stream);
+    return;
+  }
+  if (A.interp == MT_INTERP_TSC) {
+    launch_trace_bs<T, 128, MT_INTERP_TSC>(tree, C, dirs, O, A, stream);
+    return;
+  }
   switch (tree->launch_block) {
-    case 64: launch_trace_bs<T, 64>(tree, C, dirs, O, A, stream); break;
-    case 256: launch_trace_bs<T, 256>(tree, C, dirs, O, A, stream); break;
-    default: launch_trace_bs<T, 128>(tree, C, dirs, O, A, stream); break;
+    case 64: launch_trace_bs<T, 64, MT_INTERP_CIC>(tree, C, dirs, O, A, stream); break;
+    case 256: launch_trace_bs<T, 256, MT_INTERP_CIC>(tree, C, dirs, O, A, stream); break;
+    default: launch_trace_bs<T, 128, MT_INTERP_CIC>(tree, C, dirs, O, A, stream); break;
   }
 }
 
@@ -120,6 +134,7 @@ namespace mt {
 mt_status check_trace_params(const mt_trace_params* p, int64_t n_rays) {
   if (!p || n_rays < 0) return MT_ERR_INVALID_ARG;
   if (p->n_cones < 1 || p->n_cones > kMaxCones || p->steps_per_cell < 1 || p->max_steps < 1) return MT_ERR_INVALID_ARG;
+  if (p->interp < MT_INTERP_CIC || p->interp > MT_INTERP_TSC) return MT_ERR_INVALID_ARG;
   if (!p->observer || !p->z_max || !p->ray_begin) return MT_ERR_INVALID_ARG;
   if (p->ray_begin[0] != 0 || p->ray_begin[p->n_cones] != n_rays) return MT_ERR_INVALID_ARG;
   for (int c = 0; c < p->n_cones; ++c) {
@@ -161,6 +176,8 @@ extern "C" mt_status mt_trace_rays(const mt_octree* tree, const mt_trace_params*
                out->d_a, out->d_l, out->phi_o, out->phi_s, out->isw, out->n_steps, out->level, out->status, out->xi};
   TraceArgs A;
   A.steps_per_cell = params->steps_per_cell;
+  A.interp = params->interp;
+  A.pad = 0;
   A.gravity_on = params->gravity_on ? 1 : 0;
   A.max_steps = params->max_steps;
   A.n_rays = n_rays;

@@ -28,13 +28,22 @@ struct TraceArgs {
   int gravity_on;
   long long max_steps;
   long long n_rays;
+  int interp;  // MT_INTERP_*
+  int pad;
 };
+
+// The octree's field as a kernel argument, carrying the trace's interpolation scheme.
+inline DevField launch_field(const mt_octree* tree, const TraceArgs& A) {
+  DevField f = tree->f;
+  f.interp = A.interp;
+  return f;
+}
 
 constexpr int kBlock = 128;
 
 // Geodesic right-hand side.  Returns false outside a non-periodic domain.  When lf is
 // non-null it receives the most refined level containing the point.
-template <class T>
+template <class T, int IP = MT_INTERP_CIC>
 __device__ __forceinline__ bool geodesic_rhs(const DevField& F, bool grav, const double* y, double* dy, int* lf,
                                              unsigned* err) {
   double H;
@@ -44,7 +53,7 @@ __device__ __forceinline__ bool geodesic_rhs(const DevField& F, bool grav, const
   T phi = (T)0, g[3] = {(T)0, (T)0, (T)0}, pe = (T)0;
   if (grav) {
     int l;
-    if (!sample_field<T>(F, y, y[3], &phi, g, &pe, &l, err)) return false;
+    if (!sample_field<T, IP>(F, y, y[3], &phi, g, &pe, &l, err)) return false;
     if (lf) *lf = l;
   } else if (lf) {
     double u[3];
@@ -103,7 +112,7 @@ __device__ __noinline__ RayState ray_start(const DevField& F, const double* xo, 
   if (grav) {
     T p, g[3], pe;
     int l;
-    if (sample_field<T>(F, r.xo, F.eta_o, &p, g, &pe, &l, err)) phi_o = (double)p;
+    if (sample_field<T, kInterpRuntime>(F, r.xo, F.eta_o, &p, g, &pe, &l, err)) phi_o = (double)p;
   }
   const double kn = sqrt((1.0 + 2.0 * phi_o) / (1.0 - 2.0 * phi_o));
   r.y[0] = r.xo[0];
@@ -126,7 +135,7 @@ __device__ __noinline__ RayState ray_start(const DevField& F, const double* xo, 
 // One RK4 step (Sect. 2.2).  Returns true when the ray is finished.
 // One RK4 step in FP64 arithmetic with T-precision field records.  Returns true when the ray
 // is finished.
-template <class T>
+template <class T, int IP = MT_INTERP_CIC>
 __device__ __forceinline__ bool ray_step_fp64(const DevField& F, const TraceArgs& A, RayState& r, unsigned* err) {
   // a ray that starts on or past its stop surface takes no step; afterwards only the
   // shortened last step ends the ray (a full step that overshoots eta_stop is followed by
@@ -139,7 +148,7 @@ __device__ __forceinline__ bool ray_step_fp64(const DevField& F, const TraceArgs
   const bool grav = A.gravity_on != 0;
   double k[10], acc[10], t[10];
   int lf = 0;
-  if (!geodesic_rhs<T>(F, grav, r.y, k, &lf, err)) {
+  if (!geodesic_rhs<T, IP>(F, grav, r.y, k, &lf, err)) {
     r.status = MT_RAY_LEFT_DOMAIN;
     return true;
   }
@@ -157,7 +166,7 @@ __device__ __forceinline__ bool ray_step_fp64(const DevField& F, const TraceArgs
     acc[i] = r.y[i] + h6 * k[i];
     t[i] = r.y[i] + h2 * k[i];
   }
-  if (!geodesic_rhs<T>(F, grav, t, k, nullptr, err)) {
+  if (!geodesic_rhs<T, IP>(F, grav, t, k, nullptr, err)) {
     r.status = MT_RAY_LEFT_DOMAIN;
     return true;
   }
@@ -166,7 +175,7 @@ __device__ __forceinline__ bool ray_step_fp64(const DevField& F, const TraceArgs
     acc[i] += h3 * k[i];
     t[i] = r.y[i] + h2 * k[i];
   }
-  if (!geodesic_rhs<T>(F, grav, t, k, nullptr, err)) {
+  if (!geodesic_rhs<T, IP>(F, grav, t, k, nullptr, err)) {
     r.status = MT_RAY_LEFT_DOMAIN;
     return true;
   }
@@ -175,7 +184,7 @@ __device__ __forceinline__ bool ray_step_fp64(const DevField& F, const TraceArgs
     acc[i] += h3 * k[i];
     t[i] = r.y[i] + h * k[i];
   }
-  if (!geodesic_rhs<T>(F, grav, t, k, nullptr, err)) {
+  if (!geodesic_rhs<T, IP>(F, grav, t, k, nullptr, err)) {
     r.status = MT_RAY_LEFT_DOMAIN;
     return true;
   }
@@ -196,13 +205,13 @@ __device__ __forceinline__ bool ray_step_fp64(const DevField& F, const TraceArgs
 
 // One RK4 step of the trace kernels: FP64 fields integrate in FP64; FP32 fields use the
 // mixed-precision step (mt_mixed.cuh).
-template <class T>
+template <class T, int IP = MT_INTERP_CIC>
 __device__ __forceinline__ bool ray_step(const DevField& F, const TraceArgs& A, RayState& r, unsigned* err,
                                          const LaneCache* lc = nullptr) {
   if constexpr (sizeof(T) == 4) {
-    return ray_step_mixed(F, A, r, err, lc);
+    return ray_step_mixed<IP>(F, A, r, err, lc);
   } else {
-    return ray_step_fp64<T>(F, A, r, err);
+    return ray_step_fp64<T, IP>(F, A, r, err);
   }
 }
 
@@ -219,7 +228,7 @@ __device__ __noinline__ void ray_finish(const DevField& F, const TraceArgs& A, c
   if (A.gravity_on && r.status != MT_RAY_NONFINITE) {
     T p, g[3], pe;
     int l;
-    if (sample_field<T>(F, y, y[3], &p, g, &pe, &l, err)) phi_s = (double)p;
+    if (sample_field<T, kInterpRuntime>(F, y, y[3], &p, g, &pe, &l, err)) phi_s = (double)p;
   }
   const double dx = y[0] - r.xo[0], dy = y[1] - r.xo[1], dz = y[2] - r.xo[2];
   const double chi = sqrt(dx * dx + dy * dy + dz * dz);
@@ -259,6 +268,33 @@ __device__ __noinline__ void ray_finish(const DevField& F, const TraceArgs& A, c
     O.xi[ray] = y[0] - (y[5] / y[4]) * de;
     O.xi[n + ray] = y[1] - (y[6] / y[4]) * de;
     O.xi[2 * n + ray] = y[2] - (y[7] / y[4]) * de;
+  }
+}
+
+// Distortion matrix outputs: jac [4][n] = A11, A12, A21, A22 and lens [5][n] = kappa, gamma1,
+// gamma2, omega and 1/mu = det A from the decomposition of Eq. (11),
+// A = R(omega) [[1 - kappa - gamma1, -gamma2], [-gamma2, 1 - kappa + gamma1]].
+__device__ __forceinline__ void write_distortion(double A11, double A12, double A21, double A22, long long ray,
+                                                 long long n, double* jac, double* lens) {
+  if (jac) {
+    jac[ray] = A11;
+    jac[n + ray] = A12;
+    jac[2 * n + ray] = A21;
+    jac[3 * n + ray] = A22;
+  }
+  if (lens) {
+    const double tr = A11 + A22, an = A21 - A12;
+    const double om = atan2(an, tr);
+    const double one_k = 0.5 * sqrt(tr * tr + an * an);
+    double so, co;
+    sincos(om, &so, &co);
+    const double S11 = co * A11 + so * A21, S12 = co * A12 + so * A22;
+    const double S21 = -so * A11 + co * A21, S22 = -so * A12 + co * A22;
+    lens[ray] = 1.0 - one_k;
+    lens[n + ray] = 0.5 * (S22 - S11);
+    lens[2 * n + ray] = -0.5 * (S12 + S21);
+    lens[3 * n + ray] = om;
+    lens[4 * n + ray] = A11 * A22 - A12 * A21;
   }
 }
 

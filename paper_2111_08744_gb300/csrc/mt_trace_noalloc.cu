@@ -37,7 +37,7 @@ std::mutex g_mu;
 unsigned long long* g_scratch_addr[kMaxDevices];  // device address of g_noalloc_scratch per device
 unsigned long long g_host_table[kScratchWords - kHeaderWords];  // staging of the cone table (host)
 
-template <class T>
+template <class T, int IP>
 __global__ void __launch_bounds__(kBlock, 4) trace_kernel_noalloc(DevField F, int n_cones, const double* __restrict__ dirs,
                                                                OutPtrs O, TraceArgs A, unsigned long long* scratch,
                                                                unsigned* err) {
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kBlock, 4) trace_kernel_noalloc(DevField F, in
     const bool alive = ray >= 0;
     if (!__any_sync(0xffffffffu, alive)) break;
     if (alive) {
-      if (ray_step<T>(F, A, r, err)) {
+      if (ray_step<T, IP>(F, A, r, err)) {
         ray_finish<T>(F, A, r, ray, n, O, err);
         ray = -1;
       }
@@ -85,21 +85,40 @@ __global__ void __launch_bounds__(kBlock, 4) trace_kernel_noalloc(DevField F, in
   }
 }
 
-template <class T>
+template <class T, int IP>
 int noalloc_blocks_per_sm() {
   static int cached = -1;
   if (cached < 0) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel_noalloc<T>, kBlock, 0) != cudaSuccess || b < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel_noalloc<T, IP>, kBlock, 0) != cudaSuccess ||
+        b < 1)
       b = 1;
     cached = b;
   }
   return cached;
 }
 
+template <class T, int IP>
+void launch_noalloc(const mt_octree* tree, int n_cones, const double* dirs, const OutPtrs& O, const TraceArgs& A,
+                    unsigned long long* scratch, unsigned* err, cudaStream_t stream) {
+  const int grid = tree->num_sms * noalloc_blocks_per_sm<T, IP>();
+  trace_kernel_noalloc<T, IP><<<grid, kBlock, 0, stream>>>(launch_field(tree, A), n_cones, dirs, O, A, scratch, err);
+}
+
+template <class T>
+void launch_noalloc_scheme(const mt_octree* tree, int n_cones, const double* dirs, const OutPtrs& O,
+                           const TraceArgs& A, unsigned long long* scratch, unsigned* err, cudaStream_t stream) {
+  switch (A.interp) {
+    case MT_INTERP_NGP: launch_noalloc<T, MT_INTERP_NGP>(tree, n_cones, dirs, O, A, scratch, err, stream); break;
+    case MT_INTERP_TSC: launch_noalloc<T, MT_INTERP_TSC>(tree, n_cones, dirs, O, A, scratch, err, stream); break;
+    default: launch_noalloc<T, MT_INTERP_CIC>(tree, n_cones, dirs, O, A, scratch, err, stream); break;
+  }
+}
+
 mt_status check_noalloc_params(const mt_trace_params* p, int64_t n_rays) {
   if (!p || n_rays < 0) return MT_ERR_INVALID_ARG;
   if (p->n_cones < 1 || p->steps_per_cell < 1 || p->max_steps < 1) return MT_ERR_INVALID_ARG;
+  if (p->interp < MT_INTERP_CIC || p->interp > MT_INTERP_TSC) return MT_ERR_INVALID_ARG;
   if (p->n_cones > kNoAllocMaxCones) return MT_ERR_UNSUPPORTED;
   if (!p->observer || !p->z_max || !p->ray_begin) return MT_ERR_INVALID_ARG;
   if (p->ray_begin[0] != 0 || p->ray_begin[p->n_cones] != n_rays) return MT_ERR_INVALID_ARG;
@@ -166,16 +185,16 @@ extern "C" mt_status mt_trace_rays_noalloc(const mt_octree* tree, const mt_trace
                    out->d_a, out->d_l, out->phi_o, out->phi_s, out->isw, out->n_steps, out->level, out->status, out->xi};
       TraceArgs A;
       A.steps_per_cell = params->steps_per_cell;
+      A.interp = params->interp;
+      A.pad = 0;
       A.gravity_on = params->gravity_on ? 1 : 0;
       A.max_steps = params->max_steps;
       A.n_rays = n_rays;
       unsigned* err = (unsigned*)(tree->ws + 1);  // the octree's status word, read by mt_device_status
       if (tree->precision == MT_FIELD_FP64) {
-        int grid = tree->num_sms * noalloc_blocks_per_sm<double>();
-        trace_kernel_noalloc<double><<<grid, kBlock, 0, stream>>>(tree->f, params->n_cones, dirs, O, A, scratch, err);
+        launch_noalloc_scheme<double>(tree, params->n_cones, dirs, O, A, scratch, err, stream);
       } else {
-        int grid = tree->num_sms * noalloc_blocks_per_sm<float>();
-        trace_kernel_noalloc<float><<<grid, kBlock, 0, stream>>>(tree->f, params->n_cones, dirs, O, A, scratch, err);
+        launch_noalloc_scheme<float>(tree, params->n_cones, dirs, O, A, scratch, err, stream);
       }
       e = cudaGetLastError();
     }

@@ -9,7 +9,8 @@ FLOORS = {"x": 1.0, "k": 1.0, "eta": 1.0, "lambda": 1.0, "chi": 1.0, "path": 1.0
           "z0": 1e-6, "z1": 1e-6, "z4": 1e-6, "z5": 1e-6, "phi_o": 1e-6, "phi_s": 1e-6, "isw": 1e-6}
 
 
-def run_gpu(w, precision="fp64", dirs=None, gravity_on=True, max_steps=None, levels=None, ray_begin=None):
+def run_gpu(w, precision="fp64", dirs=None, gravity_on=True, max_steps=None, levels=None, ray_begin=None,
+            interp="cic"):
     import torch
 
     from paper_2111_08744_gb300 import binding as B
@@ -18,7 +19,7 @@ def run_gpu(w, precision="fp64", dirs=None, gravity_on=True, max_steps=None, lev
     lv = w.levels if levels is None else levels
     tree = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, lv, w.bg, precision)
     d = w.dirs if dirs is None else dirs
-    p = B.TraceParams.from_workload(w, gravity_on=gravity_on, max_steps=max_steps,
+    p = B.TraceParams.from_workload(w, gravity_on=gravity_on, max_steps=max_steps, interp=interp,
                                     ray_begin=ray_begin if ray_begin is not None else
                                     (None if dirs is None else np.array([0, d.shape[1]])))
     out = B.trace_rays(tree, p, torch.from_numpy(np.ascontiguousarray(d)).cuda())
