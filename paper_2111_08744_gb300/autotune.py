@@ -48,7 +48,7 @@ def autotune(tree: B.Octree, params: B.TraceParams, dirs: torch.Tensor, sample: 
     cone = np.searchsorted(begin, idx, side="right") - 1
     counts = np.bincount(cone, minlength=len(begin) - 1)
     sp = B.TraceParams(params.obs, params.zmax, np.concatenate([[0], np.cumsum(counts)]), params.c.steps_per_cell,
-                       bool(params.c.gravity_on), params.c.max_steps)
+                       bool(params.c.gravity_on), params.c.max_steps, params.interp)
     sd = dirs[:, torch.from_numpy(idx).to(dirs.device)].contiguous()
     out = B.alloc_outputs(m, dirs.device, names=["n_steps"])
     times = {}

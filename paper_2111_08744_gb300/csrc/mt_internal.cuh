@@ -62,6 +62,7 @@ struct DevField {
   float dx0_f;        // dx_0
   float bg_inv_deta_f;
   float inv_dseta[kMaxSlices];  // 1 / (eta_{s+1} - eta_s)
+  float seta_rel_f[kMaxSlices]; // eta_s - bg_eta0 (the mixed step's slice bracket)
   const unsigned* refbits;      // one bit per coarse cell (Morton order): has children on level 1
 };
 

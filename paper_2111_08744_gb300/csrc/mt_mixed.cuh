@@ -375,19 +375,22 @@ __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const Mi
 }
 
 // Step-start quantities of a mixed step: finest-level base cell and fraction, background node
-// and slice bracket of eta.  False when the position is outside a non-periodic domain.
+// and slice bracket of eta.  The node and bracket come from the FP32 offset e = eta - eta_0 of the
+// table start (one FP64 subtraction): its rounding (~1e-7 e) moves H(eta) and the slice weight
+// by far less than the FP32 interpolation itself.  False when the position is outside a
+// non-periodic domain.
 __device__ __forceinline__ bool mixed_begin(const DevField& F, const double* y, MixedStep& B) {
   if (!finest_base(F, y, B.ib, B.fb)) return false;
-  const double eta = y[3];
-  const double t0 = (eta - F.bg_eta0) * F.bg_inv_deta;
-  const double jf = floor(t0);
+  const float e = (float)(y[3] - F.bg_eta0);
+  const float t0 = e * F.bg_inv_deta_f;
+  const float jf = floorf(t0);
   B.jb = (int)jf;
-  B.tb = (float)(t0 - jf);
+  B.tb = t0 - jf;
   int s = 0;
-  while (s < F.S - 2 && F.seta[s + 1] <= eta) ++s;
+  while (s < F.S - 2 && F.seta_rel_f[s + 1] <= e) ++s;
   B.sb = s;
-  B.e_lo = (float)(eta - F.seta[s]);
-  B.e_hi = F.S > 1 ? (float)(eta - F.seta[s + 1]) : 0.0f;
+  B.e_lo = e - F.seta_rel_f[s];
+  B.e_hi = F.S > 1 ? e - F.seta_rel_f[s + 1] : 0.0f;
   return true;
 }
 
@@ -468,8 +471,9 @@ __device__ bool ray_step_mixed(const DevField& F, const TraceArgsT& A, RayStateT
   r.y[7] += (double)(h * sk[2]);
   r.y[8] += (double)(h * sI);
   r.y[9] += (double)(h * ss);
-#pragma unroll
-  for (int i = 0; i < 10; ++i) finite = finite && isfinite(r.y[i]);
+  // the state stays finite while every FP32 increment does (the FP64 sums cannot overflow at
+  // these magnitudes): one FP32 test instead of ten FP64 ones
+  finite = isfinite(h + sx[0] + sx[1] + sx[2] + se + sk0 + sk[0] + sk[1] + sk[2] + sI + ss);
   r.lambda += hd;
   r.n_steps += 1;
   if (!finite) {

@@ -258,6 +258,7 @@ extern "C" mt_status mt_build_octree(const mt_grid_desc* grid, const mt_level_da
   F.dx0_f = (float)F.dx0;
   F.bg_inv_deta_f = (float)(1.0 / de);
   for (int s = 0; s + 1 < S; ++s) F.inv_dseta[s] = (float)(1.0 / (grid->slice_eta[s + 1] - grid->slice_eta[s]));
+  for (int s = 0; s < S; ++s) F.seta_rel_f[s] = (float)(grid->slice_eta[s] - F.bg_eta0);
 
   for (int l = 0; l <= L; ++l) {
     const long long n = levels[l].count;

@@ -75,7 +75,8 @@ __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCone
   }
 }
 
-// Dynamic shared memory of trace_kernel<T, BS>: the mixed path's per-thread neighbourhood cache.
+// Dynamic shared memory of trace_kernel<T, BS>: the mixed path's per-thread neighbourhood cache and
+// coarse refinement bit (276 B per thread).
 template <class T, int BS>
 constexpr size_t trace_smem() {
   return sizeof(T) == 4 ? (size_t)BS * (16 * sizeof(float4) + sizeof(int4) + sizeof(int)) : 0;
