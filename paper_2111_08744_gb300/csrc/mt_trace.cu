@@ -1,9 +1,11 @@
 // Null-geodesic integration (Sect. 2.2): one ray per thread, persistent warps.
 //
-// Each warp keeps 32 rays in flight.  A lane whose ray has finished takes the next
-// ray id from a device-wide counter (one atomic per warp and refill), so rays of very
-// different step counts (AMR levels, cones to different z_max) keep the lanes busy
-// until the queue is empty.
+// Each warp keeps 32 rays in flight.  A lane whose ray has finished takes the next id of
+// the warp's current chunk of kRayChunk consecutive ray ids; an empty chunk is refilled from a
+// device-wide counter (one atomic per chunk).  Rays of very different step counts (AMR
+// levels, cones to different z_max) keep the lanes busy until the queue is empty, and a warp's
+// rays stay neighbours in the input order (HEALPix NESTED: nearby on the sky), so their field
+// gathers share cache lines.
 //
 // Per RK4 stage: coarse coordinates -> most refined level (hash probes) -> CIC with
 // level fallback -> geodesic right-hand side, Eqs. (2)-(4) (mt_trace_device.cuh).
@@ -15,6 +17,10 @@
 #include "mt_trace_device.cuh"
 
 namespace mt {
+
+// Ray ids a warp claims at a time: one lane's worth per lane.  Larger chunks leave warps holding
+// unstarted rays at the end of the queue (a tail with the rest of the GPU idle).
+constexpr int kRayChunk = 32;
 
 template <class T>
 __device__ void ray_init(const DevField& F, const DevCones& C, const double* __restrict__ dirs, long long n,
@@ -45,16 +51,31 @@ __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCone
   RayState r;
   long long ray = -1;
   bool exhausted = false;
+  unsigned long long pool = 0;  // next id of this warp's current chunk (warp-uniform)
+  int pool_left = 0;            // ids left in it
   for (;;) {
     const bool need = (ray < 0) && !exhausted;
     const unsigned m = __ballot_sync(0xffffffffu, need);
     if (m) {
       const int leader = __ffs(m) - 1;
-      unsigned long long base = 0;
-      if ((int)lane == leader) base = atomicAdd(ws, (unsigned long long)__popc(m));
-      base = __shfl_sync(0xffffffffu, base, leader);
+      const int k = __popc(m);
+      const int from_pool = k < pool_left ? k : pool_left;
+      unsigned long long fresh = 0;
+      if (k > from_pool) {
+        if ((int)lane == leader) fresh = atomicAdd(ws, (unsigned long long)kRayChunk);
+        fresh = __shfl_sync(0xffffffffu, fresh, leader);
+      }
+      const int rank = __popc(m & ((1u << lane) - 1u));
+      const unsigned long long pick = rank < from_pool ? pool + rank : fresh + (rank - from_pool);
+      if (k > from_pool) {
+        pool = fresh + (k - from_pool);
+        pool_left = kRayChunk - (k - from_pool);
+      } else {
+        pool += k;
+        pool_left -= k;
+      }
       if (need) {
-        const long long id = (long long)base + __popc(m & ((1u << lane) - 1u));
+        const long long id = (long long)pick;
         if (id < n) {
           ray = id;
           ray_init<T>(F, C, dirs, n, ray, grav, r, err);
