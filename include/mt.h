@@ -254,6 +254,26 @@ mt_status mt_trace_rays_lensing(const mt_octree* tree, const mt_trace_params* pa
                                 int64_t n_rays, const mt_ray_out* out, double* jac, double* lens, void* stream);
 
 /*
+ * mt_trace_beams -- the finite-beam distortion matrix of Sect. 2.3.2 (Eqs. 17-21) for each of
+ * n_beams central directions dirs[:, i]: the central ray and four rays at semi-aperture eps,
+ * along n +- tan(eps) e_1 (A, B) and n -+ tan(eps) e_2 (C, D) (normalised; e_1 = e_phi,
+ * e_2 = -e_theta of n), all stopped on the cone's iso-eta surface with their end points moved
+ * along k onto it (xi).  With the screen basis (e~_1, e~_2) of v = xi_central - x_o
+ * (screen = 0, beta-screen) or of the central ray's end wave vector (screen = 1, Sachs screen)
+ * and chi = |xi_central - x_o|:
+ *   A_a1 = (xi_A - xi_B) . e~_a / (2 chi tan eps),  A_a2 = (xi_D - xi_C) . e~_a / (2 chi tan eps)
+ * (the second column as xi_D - xi_C, so that A is the identity without gravity).  jac: device
+ * [4][N] = A11, A12, A21, A22; lens: device [5][N] = kappa, gamma_1, gamma_2, omega, det A
+ * (Eq. 11); at least one non-NULL.  `out` receives the central rays' outputs.  The rays advance
+ * as in mt_trace_rays (same step and precision rules, params->interp honoured); each GPU lane
+ * integrates one beam's five rays in turn, so nothing is allocated.  Asynchronous.
+ * Errors: as mt_trace_rays; MT_ERR_INVALID_ARG if eps is not in (0, 0.5) rad, screen is not 0 or
+ * 1, or jac and lens are both NULL.
+ */
+mt_status mt_trace_beams(const mt_octree* tree, const mt_trace_params* params, const double* dirs, int64_t n_beams,
+                         double eps, int32_t screen, const mt_ray_out* out, double* jac, double* lens, void* stream);
+
+/*
  * mt_pullback_coarse_phi -- dL/dphi_0 on the coarse grid from record cotangents dL_drec
  * (as accumulated by mt_trace_rays_adjoint), through this library's field model:
  *   coarse records  = w_s (phi_0, D phi_0), D the periodic 5-point central difference

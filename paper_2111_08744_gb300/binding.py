@@ -84,6 +84,9 @@ def load():
         lib.mt_trace_rays_lensing.restype = ctypes.c_int
         lib.mt_trace_rays_lensing.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64,
                                               ctypes.POINTER(mt_ray_out), P, P, P]
+        lib.mt_trace_beams.restype = ctypes.c_int
+        lib.mt_trace_beams.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64, ctypes.c_double,
+                                       ctypes.c_int32, ctypes.POINTER(mt_ray_out), P, P, P]
         lib.mt_pullback_coarse_phi.restype = ctypes.c_int
         lib.mt_pullback_coarse_phi.argtypes = [P, ctypes.POINTER(P), P, P, P]
         lib.mt_trace_rays_noalloc.restype = ctypes.c_int
@@ -364,6 +367,29 @@ def trace_rays_lensing(tree: Octree, params: TraceParams, dirs, out=None, stream
     _check(load().mt_trace_rays_lensing(tree.handle, ctypes.byref(params.c), dirs.data_ptr(), n, ctypes.byref(o),
                                         jac.data_ptr(), lens.data_ptr(), _stream_handle(stream)),
            "mt_trace_rays_lensing")
+    res = dict(out)
+    res["jac"] = jac
+    res["lens"] = lens
+    return res
+
+
+def mt_trace_beams(tree, params, dirs, n_beams, eps, screen, out, jac, lens, stream):
+    return load().mt_trace_beams(tree, params, dirs, n_beams, eps, screen, out, jac, lens, stream)
+
+
+def trace_beams(tree: Octree, params: TraceParams, dirs, eps=1e-6, screen=0, out=None, stream=None):
+    """mt_trace_beams on CUDA tensors: the central rays' outputs plus the finite-beam distortion
+    matrix "jac" [4, N] and "lens" [5, N] (Eqs. 17-21; screen 0: beta-screen, 1: Sachs screen)."""
+    torch = _require_cuda()
+    n = int(dirs.shape[1])
+    if out is None:
+        out = alloc_outputs(n, dirs.device)
+    jac = torch.empty((4, n), dtype=torch.float64, device=dirs.device)
+    lens = torch.empty((5, n), dtype=torch.float64, device=dirs.device)
+    o = ray_out_struct(out)
+    _check(load().mt_trace_beams(tree.handle, ctypes.byref(params.c), dirs.data_ptr(), n, float(eps), int(screen),
+                                 ctypes.byref(o), jac.data_ptr(), lens.data_ptr(), _stream_handle(stream)),
+           "mt_trace_beams")
     res = dict(out)
     res["jac"] = jac
     res["lens"] = lens

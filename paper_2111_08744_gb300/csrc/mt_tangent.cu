@@ -318,20 +318,6 @@ __device__ bool tangent_step_mixed(const DevField& F, const TraceArgs& A, RaySta
   return last;
 }
 
-__device__ void screen_vectors(const double* v, double* e1, double* e2) {
-  const double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-  const double t1 = atan2(v[1], v[0]);
-  const double t2 = acos(fmin(1.0, fmax(-1.0, v[2] / n)));
-  double s1, c1, s2, c2;
-  sincos(t1, &s1, &c1);
-  sincos(t2, &s2, &c2);
-  e1[0] = -s1;
-  e1[1] = c1;
-  e1[2] = 0.0;
-  e2[0] = -c1 * c2;
-  e2[1] = -s1 * c2;
-  e2[2] = s2;
-}
 
 __device__ __noinline__ void tangent_finish(const RayState r, const TanState ts, long long ray, long long n,
                                             double* jac, double* lens) {

@@ -97,12 +97,11 @@ struct RayState {
   int status;
 };
 
-// Initial state of a ray leaving observer xo at eta_o along dirs[:, ray] (Sect. 2.2):
+// Initial state of a ray leaving observer xo at eta_o along the unit direction nd (Sect. 2.2):
 // k0 = -1 and k^i = n sqrt((1 + 2 phi_o)/(1 - 2 phi_o)) (null condition of Eq. 1).
 template <class T>
-__device__ __noinline__ RayState ray_start(const DevField& F, const double* xo, double eta_stop,
-                                           const double* __restrict__ dirs, long long n, long long ray, bool grav,
-                                           unsigned* err) {
+__device__ __noinline__ RayState ray_start_dir(const DevField& F, const double* xo, double eta_stop, const double* nd,
+                                               bool grav, unsigned* err) {
   RayState r;
   r.xo[0] = xo[0];
   r.xo[1] = xo[1];
@@ -120,9 +119,9 @@ __device__ __noinline__ RayState ray_start(const DevField& F, const double* xo, 
   r.y[2] = r.xo[2];
   r.y[3] = F.eta_o;
   r.y[4] = -1.0;
-  r.y[5] = __ldg(&dirs[ray]) * kn;
-  r.y[6] = __ldg(&dirs[n + ray]) * kn;
-  r.y[7] = __ldg(&dirs[2 * n + ray]) * kn;
+  r.y[5] = nd[0] * kn;
+  r.y[6] = nd[1] * kn;
+  r.y[7] = nd[2] * kn;
   r.y[8] = 0.0;
   r.y[9] = 0.0;
   r.lambda = 0.0;
@@ -130,6 +129,15 @@ __device__ __noinline__ RayState ray_start(const DevField& F, const double* xo, 
   r.n_steps = 0;
   r.status = MT_RAY_OK;
   return r;
+}
+
+// The same along dirs[:, ray] ([3][n], structure of arrays).
+template <class T>
+__device__ __noinline__ RayState ray_start(const DevField& F, const double* xo, double eta_stop,
+                                              const double* __restrict__ dirs, long long n, long long ray, bool grav,
+                                              unsigned* err) {
+  const double nd[3] = {__ldg(&dirs[ray]), __ldg(&dirs[n + ray]), __ldg(&dirs[2 * n + ray])};
+  return ray_start_dir<T>(F, xo, eta_stop, nd, grav, err);
 }
 
 // One RK4 step (Sect. 2.2).  Returns true when the ray is finished.
@@ -269,6 +277,23 @@ __device__ __noinline__ void ray_finish(const DevField& F, const TraceArgs& A, c
     O.xi[n + ray] = y[1] - (y[6] / y[4]) * de;
     O.xi[2 * n + ray] = y[2] - (y[7] / y[4]) * de;
   }
+}
+
+// Screen basis of Sect. 2.3.2 for the direction v (any length): e1 = e_phi = (-sin p, cos p, 0),
+// e2 = -e_theta = (-cos p cos t, -sin p cos t, sin t) with p = atan2(v_y, v_x), t = acos(v_z / |v|).
+__device__ __forceinline__ void screen_vectors(const double* v, double* e1, double* e2) {
+  const double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  const double t1 = atan2(v[1], v[0]);
+  const double t2 = acos(fmin(1.0, fmax(-1.0, v[2] / n)));
+  double s1, c1, s2, c2;
+  sincos(t1, &s1, &c1);
+  sincos(t2, &s2, &c2);
+  e1[0] = -s1;
+  e1[1] = c1;
+  e1[2] = 0.0;
+  e2[0] = -c1 * c2;
+  e2[1] = -s1 * c2;
+  e2[2] = s2;
 }
 
 // Distortion matrix outputs: jac [4][n] = A11, A12, A21, A22 and lens [5][n] = kappa, gamma1,
