@@ -80,6 +80,9 @@ def _load():
             lib.orc_infinitesimal.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Level), ctypes.c_void_p,
                                               ctypes.c_int, ctypes.POINTER(_Params), ctypes.c_void_p, ctypes.c_int64,
                                               ctypes.c_void_p, ctypes.c_int]
+            lib.orc_healpix_pixels.restype = None
+            lib.orc_healpix_pixels.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                               ctypes.c_void_p]
             lib.orc_sample.restype = ctypes.c_int
             lib.orc_sample.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Level), ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
@@ -217,6 +220,16 @@ def sample(w, pts, eta, levels=None, interp="cic"):
     if rc != 0:
         raise RuntimeError(f"oracle sample failed with code {rc}")
     return phi, grad, pe, lf, lc
+
+
+def healpix_pixels(dirs, nside, nest=True):
+    """HEALPix pixel index (NESTED or RING) of each direction [3, n] (Gorski et al. 2005)."""
+    lib = _load()
+    d = np.ascontiguousarray(dirs, dtype=np.float64)
+    n = int(d.shape[1])
+    pix = np.zeros(n, dtype=np.int64)
+    lib.orc_healpix_pixels(_ptr(d), n, int(nside), 1 if nest else 0, _ptr(pix))
+    return pix
 
 
 def eta_stop(bg, z):

@@ -629,6 +629,67 @@ int orc_trace(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n
   return 0;
 }
 
+// HEALPix pixel of direction v (Gorski et al. 2005, the sky pixelisation of Sect. 2.5): z = cos(theta),
+// t = phi / (pi/2) in [0, 4).  Equatorial zone |z| <= 2/3: the pixel is fixed by the two edge-line
+// indices jp = floor(N (1/2 + t) - 3N z / 4) and jm = floor(N (1/2 + t) + 3N z / 4); polar caps: by
+// jp = floor(tp s), jm = floor((1 - tp) s) with s = N sqrt(3 (1 - |z|)), tp the position in the
+// quarter.  RING numbers rings from the north pole; NESTED numbers the 12 base faces and
+// interleaves the in-face (x, y) bits.
+static int64_t healpix_pixel(int64_t N, const double* v, bool nest) {
+  double r = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  double z = v[2] / r, za = std::fabs(z);
+  double ph = std::atan2(v[1], v[0]);
+  const double pi = 3.14159265358979323846;
+  if (ph < 0.0) ph += 2.0 * pi;
+  double t = ph / (0.5 * pi);
+  if (t >= 4.0) t -= 4.0;
+  int64_t npix = 12 * N * N, ncap = 2 * N * (N - 1);
+  if (za <= 2.0 / 3.0) {
+    double a = N * (0.5 + t), b = 0.75 * N * z;
+    int64_t jp = (int64_t)std::floor(a - b), jm = (int64_t)std::floor(a + b);
+    if (!nest) {
+      int64_t ir = N + 1 + jp - jm;                 // ring counted from z = 2/3, 1 .. 2N + 1
+      int64_t shift = 1 - (ir & 1);
+      int64_t ip = (jp + jm - N + shift + 1) / 2;
+      ip = ((ip % (4 * N)) + 4 * N) % (4 * N);
+      return ncap + (ir - 1) * 4 * N + ip;
+    }
+    int64_t fp = jp / N, fm = jm / N;
+    int64_t face = fp == fm ? (fp | 4) : (fp < fm ? fp : fm + 8);
+    int64_t ix = jm & (N - 1), iy = N - (jp & (N - 1)) - 1;
+    int64_t pix = 0;
+    for (int b2 = 0; b2 < 31; ++b2) pix |= (((ix >> b2) & 1) << (2 * b2)) | (((iy >> b2) & 1) << (2 * b2 + 1));
+    return face * N * N + pix;
+  }
+  int64_t q = (int64_t)t;
+  if (q > 3) q = 3;
+  double tp = t - (double)q;
+  double sc = N * std::sqrt(3.0 * (1.0 - za));
+  int64_t jp = (int64_t)(tp * sc), jm = (int64_t)((1.0 - tp) * sc);
+  if (!nest) {
+    int64_t ir = jp + jm + 1;                       // ring counted from the nearer pole
+    int64_t ip = (int64_t)(t * ir);
+    ip = ((ip % (4 * ir)) + 4 * ir) % (4 * ir);
+    return z > 0 ? 2 * ir * (ir - 1) + ip : npix - 2 * ir * (ir + 1) + ip;
+  }
+  if (jp > N - 1) jp = N - 1;
+  if (jm > N - 1) jm = N - 1;
+  int64_t face, ix, iy;
+  if (z > 0) { face = q; ix = N - jm - 1; iy = N - jp - 1; }
+  else { face = q + 8; ix = jp; iy = jm; }
+  int64_t pix = 0;
+  for (int b2 = 0; b2 < 31; ++b2) pix |= (((ix >> b2) & 1) << (2 * b2)) | (((iy >> b2) & 1) << (2 * b2 + 1));
+  return face * N * N + pix;
+}
+
+// HEALPix pixels of n directions ([3][n]); nest: 1 NESTED, 0 RING.
+void orc_healpix_pixels(const double* v, int64_t n, int64_t nside, int nest, int64_t* pix) {
+  for (int64_t i = 0; i < n; ++i) {
+    double d[3] = {v[i], v[n + i], v[2 * n + i]};
+    pix[i] = healpix_pixel(nside, d, nest != 0);
+  }
+}
+
 // Infinitesimal-beam distortion matrix, Eq. (12) with Eqs. (13)-(16), integrated along each
 // traced ray (trapezoidal rule over the step points); with gravity off the rays are FLRW
 // trajectories: the Born approximation of Sect. 2.3.1.  A: [4][N] = A11, A12, A21, A22.
