@@ -274,6 +274,31 @@ mt_status mt_trace_beams(const mt_octree* tree, const mt_trace_params* params, c
                          double eps, int32_t screen, const mt_ray_out* out, double* jac, double* lens, void* stream);
 
 /*
+ * mt_healpix_bin -- HEALPix maps of per-ray quantities (Sect. 2.5 map products: lensing,
+ * lensing_born, deflection, phi, isw, steps, relative differences...).  Each direction
+ * dirs[:, i] (device [3][n], any length) gets its pixel at resolution nside (a power of two,
+ * <= 2^28) in the NESTED (nest = 1) or RING (nest = 0) numbering of Gorski et al. (2005), and
+ * values[q][i] (device [k][n]) is ADDED to sums[q][pix] (device [k][12 nside^2]); counts[pix]
+ * (device [12 nside^2], may be NULL) gains 1 per ray; ipix (device [n], may be NULL) receives the
+ * pixels.  The map of quantity q is sums[q] / counts.  FP64 atomics: the sums' rounding order is
+ * not fixed.  Rays shot at pixel centres map one to one.  Asynchronous on `stream`.
+ * Errors: MT_ERR_INVALID_ARG (nside, nest, NULL arrays), MT_ERR_CUDA.
+ */
+mt_status mt_healpix_bin(const double* dirs, int64_t n, const double* values, int32_t k, int64_t nside, int32_t nest,
+                         double* sums, double* counts, int64_t* ipix, void* stream);
+
+/*
+ * mt_deflection -- the deflection angle of Sect. 2.5, alpha = theta - beta, for rays traced with
+ * params (the cone table gives each ray's observer): theta = dirs[:, i] (observed direction),
+ * beta = the direction of xi[:, i] - x_o (xi: end points on the stop surface, device [3][N], as
+ * written by the trace calls).  alpha: device [3][N] = the components of theta^ - beta^ on the
+ * screen (e_phi, -e_theta) of theta, and the angle between theta and beta (rad).  Asynchronous.
+ * Errors: as mt_trace_rays's parameter checks; MT_ERR_INVALID_ARG for NULL arrays.
+ */
+mt_status mt_deflection(const mt_octree* tree, const mt_trace_params* params, const double* dirs, int64_t n_rays,
+                        const double* xi, double* alpha, void* stream);
+
+/*
  * mt_pullback_coarse_phi -- dL/dphi_0 on the coarse grid from record cotangents dL_drec
  * (as accumulated by mt_trace_rays_adjoint), through this library's field model:
  *   coarse records  = w_s (phi_0, D phi_0), D the periodic 5-point central difference

@@ -87,6 +87,10 @@ def load():
         lib.mt_trace_beams.restype = ctypes.c_int
         lib.mt_trace_beams.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64, ctypes.c_double,
                                        ctypes.c_int32, ctypes.POINTER(mt_ray_out), P, P, P]
+        lib.mt_healpix_bin.restype = ctypes.c_int
+        lib.mt_healpix_bin.argtypes = [P, ctypes.c_int64, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, P, P, P, P]
+        lib.mt_deflection.restype = ctypes.c_int
+        lib.mt_deflection.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64, P, P, P]
         lib.mt_pullback_coarse_phi.restype = ctypes.c_int
         lib.mt_pullback_coarse_phi.argtypes = [P, ctypes.POINTER(P), P, P, P]
         lib.mt_trace_rays_noalloc.restype = ctypes.c_int
@@ -394,6 +398,38 @@ def trace_beams(tree: Octree, params: TraceParams, dirs, eps=1e-6, screen=0, out
     res["jac"] = jac
     res["lens"] = lens
     return res
+
+
+def mt_healpix_bin(dirs, n, values, k, nside, nest, sums, counts, ipix, stream):
+    return load().mt_healpix_bin(dirs, n, values, k, nside, nest, sums, counts, ipix, stream)
+
+
+def healpix_bin(dirs, values=None, nside=64, nest=True, stream=None):
+    """mt_healpix_bin on CUDA tensors: dirs [3, N], values [K, N] (or None).  Returns
+    (sums [K, 12 nside^2], counts [12 nside^2], ipix [N])."""
+    torch = _require_cuda()
+    dirs = dirs.contiguous()
+    n = int(dirs.shape[1])
+    npix = 12 * int(nside) ** 2
+    k = 0 if values is None else int(values.shape[0])
+    vals = None if values is None else values.contiguous().to(torch.float64)
+    sums = torch.zeros((k, npix), dtype=torch.float64, device=dirs.device)
+    counts = torch.zeros(npix, dtype=torch.float64, device=dirs.device)
+    ipix = torch.empty(n, dtype=torch.int64, device=dirs.device)
+    _check(load().mt_healpix_bin(dirs.data_ptr(), n, vals.data_ptr() if vals is not None else None, k, int(nside),
+                                 1 if nest else 0, sums.data_ptr() if k else None, counts.data_ptr(), ipix.data_ptr(),
+                                 _stream_handle(stream)), "mt_healpix_bin")
+    return sums, counts, ipix
+
+
+def deflection(tree: Octree, params: TraceParams, dirs, xi, stream=None):
+    """mt_deflection: alpha [3, N] = screen components of theta - beta and the angle between them."""
+    torch = _require_cuda()
+    n = int(dirs.shape[1])
+    alpha = torch.empty((3, n), dtype=torch.float64, device=dirs.device)
+    _check(load().mt_deflection(tree.handle, ctypes.byref(params.c), dirs.contiguous().data_ptr(), n,
+                                xi.contiguous().data_ptr(), alpha.data_ptr(), _stream_handle(stream)), "mt_deflection")
+    return alpha
 
 
 def mt_pullback_coarse_phi(tree, dL_drec, slice_weight, dL_dphi0, stream):
