@@ -83,6 +83,10 @@ def _load():
             lib.orc_healpix_pixels.restype = None
             lib.orc_healpix_pixels.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                                ctypes.c_void_p]
+            lib.orc_trace_to_chi.restype = ctypes.c_int
+            lib.orc_trace_to_chi.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Level), ctypes.c_void_p,
+                                             ctypes.c_int, ctypes.POINTER(_Params), ctypes.c_void_p, ctypes.c_int64,
+                                             ctypes.c_void_p, ctypes.POINTER(_Out), ctypes.c_int]
             lib.orc_sample.restype = ctypes.c_int
             lib.orc_sample.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Level), ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
@@ -136,10 +140,12 @@ def _interp(interp):
 
 
 def trace(w, dirs=None, levels=None, gravity_on=True, max_steps=10_000_000, n_threads=None, ray_begin=None,
-          interp="cic"):
+          interp="cic", chi_stop=None):
     """Trace rays of workload `w` (optionally other directions / a subset). Returns a dict of arrays.
 
     interp: "cic" (Eq. 8), "ngp" (Eq. 7) or "tsc" (Eq. 9), each with the level fallback of Sect. 2.2.
+    chi_stop: per-ray comoving distances [N]: stop on the sphere |x - x_o| = chi_stop (the geodesic
+    finder's criterion, Sect. 2.6) instead of the iso-eta surface of z_max.
 
     Besides the per-ray outputs of the method, "tie" is the smallest margin of any index
     decision along the ray: the distance (in cell units) of a floor() argument to the
@@ -162,8 +168,14 @@ def trace(w, dirs=None, levels=None, gravity_on=True, max_steps=10_000_000, n_th
     out.update({k: np.zeros(n, dtype=np.int32) for k in _OUT_I32})
     out["tie"] = np.ones(n)
     o = _Out(**{k: _ptr(v) for k, v in out.items()})
-    rc = lib.orc_trace(ctypes.byref(m.grid), m.levels, _ptr(m.bg), int(m.bg.shape[0]), ctypes.byref(m.params),
-                       _ptr(d), n, ctypes.byref(o), int(n_threads or default_threads()))
+    if chi_stop is None:
+        rc = lib.orc_trace(ctypes.byref(m.grid), m.levels, _ptr(m.bg), int(m.bg.shape[0]), ctypes.byref(m.params),
+                           _ptr(d), n, ctypes.byref(o), int(n_threads or default_threads()))
+    else:
+        cs = np.ascontiguousarray(np.broadcast_to(chi_stop, (n,)), dtype=np.float64)
+        rc = lib.orc_trace_to_chi(ctypes.byref(m.grid), m.levels, _ptr(m.bg), int(m.bg.shape[0]),
+                                  ctypes.byref(m.params), _ptr(d), n, _ptr(cs), ctypes.byref(o),
+                                  int(n_threads or default_threads()))
     if rc != 0:
         raise RuntimeError(f"oracle trace failed with code {rc} (unsorted keys?)")
     return out

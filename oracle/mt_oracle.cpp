@@ -418,7 +418,12 @@ struct Tracer {
     }
   };
 
-  Result trace(const double* xo, const double* n, double eta_stop, bool inf_beam = false) const {
+  // chi_stop > 0: the iso-chi stop of the geodesic finder (Sect. 2.6): the ray steps as usual
+  // until its comoving distance |x - x_o| reaches chi_stop, and the end point is then moved back
+  // along k onto that sphere: x - t k with the smaller root t of |x - t k - x_o| = chi_stop (and
+  // eta - t k0).  eta_stop then only bounds the integration.
+  Result trace(const double* xo, const double* n, double eta_stop, bool inf_beam = false,
+               double chi_stop = -1.0) const {
     Result r;
     InfBeam ib;
     double* y = r.y;
@@ -479,6 +484,19 @@ struct Tracer {
         double chi = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         if (!screen_hessian(y, y[3], xo, fv)) fv[0] = fv[1] = fv[2] = 0.0;
         ib.add(chi, fv);
+      }
+      if (chi_stop > 0.0) {
+        double d[3] = {y[0] - xo[0], y[1] - xo[1], y[2] - xo[2]};
+        double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (dd >= chi_stop * chi_stop) {
+          double kk = y[5] * y[5] + y[6] * y[6] + y[7] * y[7];
+          double b = d[0] * y[5] + d[1] * y[6] + d[2] * y[7];
+          double c = dd - chi_stop * chi_stop;
+          double t = (b - std::sqrt(std::max(0.0, b * b - kk * c))) / kk;
+          for (int q = 0; q < 3; ++q) y[q] -= t * y[5 + q];
+          y[3] -= t * y[4];
+          break;
+        }
       }
       if (last) break;
     }
@@ -587,18 +605,19 @@ int orc_sample(const orc_grid* g, const orc_level* lv, const double* pts /*[3][n
   return 0;
 }
 
-int orc_trace(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n, const orc_params* p,
-              const double* dirs /*[3][N]*/, int64_t n_rays, orc_out* o, int n_threads) {
+static int trace_rays_impl(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n, const orc_params* p,
+                    const double* dirs /*[3][N]*/, int64_t n_rays, const double* chi_stop, orc_out* o,
+                    int n_threads) {
   if (!keys_sorted(g, lv)) return 4;
   if (p->interp < INTERP_CIC || p->interp > INTERP_TSC) return 5;
   Tracer t = make_tracer(g, lv, bg, bg_n, p);
   std::vector<double> es(p->n_cones);
-  for (int c = 0; c < p->n_cones; ++c) es[c] = t.bg.eta_stop(p->z_max[c]);
+  for (int c = 0; c < p->n_cones; ++c) es[c] = chi_stop ? bg[0] : t.bg.eta_stop(p->z_max[c]);
   parallel_for(n_rays, n_threads, [&](int64_t i) {
     int c = cone_of(p, i);
     const double* xo = p->observer + 3 * c;
     double n[3] = {dirs[i], dirs[n_rays + i], dirs[2 * n_rays + i]};
-    Tracer::Result r = t.trace(xo, n, es[c]);
+    Tracer::Result r = t.trace(xo, n, es[c], false, chi_stop ? chi_stop[i] : -1.0);
     const double* y = r.y;
     double a_s = t.bg.a_of(y[3]);
     double dxo[3] = {y[0] - xo[0], y[1] - xo[1], y[2] - xo[2]};
@@ -707,6 +726,17 @@ int orc_infinitesimal(const orc_grid* g, const orc_level* lv, const double* bg, 
     for (int q = 0; q < 4; ++q) A[q * n_rays + i] = r.A[q];
   });
   return 0;
+}
+
+int orc_trace(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n, const orc_params* p,
+              const double* dirs /*[3][N]*/, int64_t n_rays, orc_out* o, int n_threads) {
+  return trace_rays_impl(g, lv, bg, bg_n, p, dirs, n_rays, nullptr, o, n_threads);
+}
+
+// Rays stopped at the comoving distances chi_stop[i] (the geodesic finder's iso-chi surface, Sect. 2.6).
+int orc_trace_to_chi(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n, const orc_params* p,
+                     const double* dirs, int64_t n_rays, const double* chi_stop, orc_out* o, int n_threads) {
+  return trace_rays_impl(g, lv, bg, bg_n, p, dirs, n_rays, chi_stop, o, n_threads);
 }
 
 // Finite-beam distortion matrix, Eqs. (17)-(21): four rays at semi-aperture eps around

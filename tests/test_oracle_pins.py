@@ -399,3 +399,30 @@ def test_step_size_follows_refinement_level():
     d0 = np.linalg.norm(oracle.xi_on_surface(o0, es) - w0.observer[0][:, None], axis=0)
     d2 = np.linalg.norm(oracle.xi_on_surface(o2, es) - w0.observer[0][:, None], axis=0)
     np.testing.assert_allclose(d2, d0, rtol=1e-11)
+
+
+# ---------------------------------------------------------------- iso-chi stop (Sect. 2.6 geodesic finder)
+
+def test_iso_chi_stop_flrw_and_constant_gradient():
+    """FLRW: the ray ends exactly on the sphere along its direction; phi = g.x: the end point on
+    the sphere |x - x_o| = chi is deflected by x_perp = -g_perp chi^2 (first order)."""
+    n, box = 16, 4000.0
+    g = np.array([2e-9, -1e-9, 1.5e-9])
+    lv = [H.coarse_level_from_fn(n, box, H.linear_fn(g, 0.0))]
+    dirs = I.healpix_directions(2)
+    w = H.workload(lv, box, n, dirs, z_max=0.4, periodic=0, steps_per_cell=8)
+    chi = np.linspace(300.0, 1400.0, dirs.shape[1])
+    x0 = w.observer[0][:, None]
+    flrw = oracle.trace(w, gravity_on=False, chi_stop=chi)
+    assert (flrw["status"] == 0).all()
+    np.testing.assert_allclose(flrw["x"], x0 + chi * dirs, rtol=0, atol=1e-9)
+    o = oracle.trace(w, chi_stop=chi)
+    d = o["x"] - x0
+    np.testing.assert_allclose(np.linalg.norm(d, axis=0), chi, rtol=1e-12)
+    along = (d * dirs).sum(0)
+    trans = d - along * dirs
+    gperp = g[:, None] - (g[:, None] * dirs).sum(0) * dirs
+    ref = -gperp * along ** 2
+    assert np.abs(trans - ref).max() / np.abs(ref).max() < 5e-3
+    # eta at the sphere: eta_o - chi in FLRW
+    np.testing.assert_allclose(flrw["eta"], w.bg[-1, 0] - chi, rtol=0, atol=1e-8)
