@@ -274,6 +274,28 @@ mt_status mt_trace_beams(const mt_octree* tree, const mt_trace_params* params, c
                          double eps, int32_t screen, const mt_ray_out* out, double* jac, double* lens, void* stream);
 
 /*
+ * mt_find_geodesics -- geodesic finder (Sect. 2.6): for each source at comoving position
+ * src[:, i] (device [3][N], absolute box coordinates; source i belongs to the cone of params,
+ * whose observer x_o it uses; z_max is ignored), the observed direction theta at x_o whose ray,
+ * stopped on the sphere |x - x_o| = chi_s = |src - x_o| (the end point moved back along k onto it),
+ * is seen from x_o in the source's direction beta.  Newton on the screen (e_phi, -e_theta) of the
+ * current direction, theta_{i+1} = theta_i - A^{-1} (beta_i - beta) (Eq. 22), with A the exact
+ * derivative of the discrete map (forward tangents) from the first iteration, until |beta_i - beta|
+ * < tol (rad); after max_newton (1..100) iterations, up to max_grid (0..64) rounds of a 5 x 5 grid
+ * around the best direction, halving its spacing each round.  Rays advance as in the trace calls;
+ * the background table's first node bounds them.  Outputs (device, length N): theta [3][N];
+ * jac [4][N] (A11, A12, A21, A22 at the solution, or NULL); resid [N] (|beta_i - beta|, or NULL);
+ * iters [N] (traces per source, or NULL); status [N]: 0 converged by Newton, 1 by the grid,
+ * 2 not converged (theta is the best found), 3 the ray failed; `out` receives the solution ray's
+ * outputs at the sphere (x on it; z0..z5, phi_s, isw at that point).  Asynchronous.
+ * Errors: as mt_trace_rays's parameter checks; MT_ERR_INVALID_ARG for tol <= 0, out-of-range
+ * iteration limits or NULL required arrays.
+ */
+mt_status mt_find_geodesics(const mt_octree* tree, const mt_trace_params* params, const double* src, int64_t n_src,
+                            double tol, int32_t max_newton, int32_t max_grid, const mt_ray_out* out, double* theta,
+                            double* jac, double* resid, int32_t* iters, int32_t* status, void* stream);
+
+/*
  * mt_healpix_bin -- HEALPix maps of per-ray quantities (Sect. 2.5 map products: lensing,
  * lensing_born, deflection, phi, isw, steps, relative differences...).  Each direction
  * dirs[:, i] (device [3][n], any length) gets its pixel at resolution nside (a power of two,

@@ -87,6 +87,9 @@ def load():
         lib.mt_trace_beams.restype = ctypes.c_int
         lib.mt_trace_beams.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64, ctypes.c_double,
                                        ctypes.c_int32, ctypes.POINTER(mt_ray_out), P, P, P]
+        lib.mt_find_geodesics.restype = ctypes.c_int
+        lib.mt_find_geodesics.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64, ctypes.c_double,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(mt_ray_out), P, P, P, P, P, P]
         lib.mt_healpix_bin.restype = ctypes.c_int
         lib.mt_healpix_bin.argtypes = [P, ctypes.c_int64, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, P, P, P, P]
         lib.mt_deflection.restype = ctypes.c_int
@@ -397,6 +400,32 @@ def trace_beams(tree: Octree, params: TraceParams, dirs, eps=1e-6, screen=0, out
     res = dict(out)
     res["jac"] = jac
     res["lens"] = lens
+    return res
+
+
+def mt_find_geodesics(tree, params, src, n, tol, max_newton, max_grid, out, theta, jac, resid, iters, status, stream):
+    return load().mt_find_geodesics(tree, params, src, n, tol, max_newton, max_grid, out, theta, jac, resid, iters,
+                                    status, stream)
+
+
+def find_geodesics(tree: Octree, params: TraceParams, src, tol=1e-9, max_newton=10, max_grid=20, stream=None):
+    """mt_find_geodesics on CUDA tensors: src [3, N] source positions.  Returns the solution rays'
+    outputs plus "theta" [3, N], "jac" [4, N], "resid" [N], "iters" [N] and "fstatus" [N]."""
+    torch = _require_cuda()
+    src = src.contiguous()
+    n = int(src.shape[1])
+    out = alloc_outputs(n, src.device)
+    theta = torch.empty((3, n), dtype=torch.float64, device=src.device)
+    jac = torch.empty((4, n), dtype=torch.float64, device=src.device)
+    resid = torch.empty(n, dtype=torch.float64, device=src.device)
+    iters = torch.empty(n, dtype=torch.int32, device=src.device)
+    status = torch.empty(n, dtype=torch.int32, device=src.device)
+    _check(load().mt_find_geodesics(tree.handle, ctypes.byref(params.c), src.data_ptr(), n, float(tol),
+                                    int(max_newton), int(max_grid), ctypes.byref(ray_out_struct(out)),
+                                    theta.data_ptr(), jac.data_ptr(), resid.data_ptr(), iters.data_ptr(),
+                                    status.data_ptr(), _stream_handle(stream)), "mt_find_geodesics")
+    res = dict(out)
+    res.update(theta=theta, jac=jac, resid=resid, iters=iters, fstatus=status)
     return res
 
 

@@ -342,9 +342,7 @@ __device__ __noinline__ void tangent_finish(const RayState r, const TanState ts,
 }
 
 // Initial tangents: the direction perturbed along the observer's screen vectors e_1, e_2.
-__device__ __noinline__ void tangent_init(const double* __restrict__ dirs, long long n, long long ray,
-                                          const RayState& r, TanState& ts) {
-  const double nd[3] = {__ldg(&dirs[ray]), __ldg(&dirs[n + ray]), __ldg(&dirs[2 * n + ray])};
+__device__ __noinline__ void tangent_init_dir(const double* nd, const RayState& r, TanState& ts) {
   double e1[3], e2[3];
   screen_vectors(nd, e1, e2);
   const double kn = sqrt(r.y[5] * r.y[5] + r.y[6] * r.y[6] + r.y[7] * r.y[7]) /
@@ -354,6 +352,12 @@ __device__ __noinline__ void tangent_init(const double* __restrict__ dirs, long 
     for (int i = 0; i < 5; ++i) ts.d[b][i] = 0.0;
     for (int d = 0; d < 3; ++d) ts.d[b][5 + d] = kn * e[d];
   }
+}
+
+__device__ __forceinline__ void tangent_init(const double* __restrict__ dirs, long long n, long long ray,
+                                             const RayState& r, TanState& ts) {
+  const double nd[3] = {__ldg(&dirs[ray]), __ldg(&dirs[n + ray]), __ldg(&dirs[2 * n + ray])};
+  tangent_init_dir(nd, r, ts);
 }
 
 template <class T, int IP>
@@ -499,6 +503,261 @@ void launch_tangent_scheme(const mt_octree* tree, const DevCones& C, const doubl
   }
 }
 
+// ----------------------------------------------------------------------------- geodesic finder
+
+// Geodesic finder (Sect. 2.6, Eq. 22): the observed direction theta whose ray, stopped on the sphere
+// |x - x_o| = chi_s of the source, is seen from the observer in the source's direction beta.
+// Newton on the screen (e_1, e_2) of theta_i:  theta_{i+1} = theta_i - A^{-1} (beta_i - beta), with
+// A = d beta / d theta the exact derivative of the discrete map (the forward tangents, projected
+// onto the sphere along k) from the first iteration; after max_newton iterations a shrinking 5 x 5
+// grid of directions around the best one.  Status: 0 Newton converged, 1 grid converged, 2 not
+// converged, 3 the ray failed (left the domain, step cap, or the background table ended first).
+struct FinderPtrs {
+  const double* src;
+  double* theta;
+  double* jac;
+  double* resid;
+  int32_t* iters;
+  int32_t* status;
+};
+
+struct SphereHit {
+  double xp[3];       // end point on the sphere
+  double dxp[2][3];   // its derivatives along the screen of theta
+};
+
+// Trace from x_o along th with tangents until |x - x_o| >= chi_s, then move the end point back along
+// k onto the sphere: xp = x - t k, t the smaller root of |x - t k - x_o| = chi_s; its tangents
+// dxp = dx - t dk - dt k with dt from the constraint (xp - x_o) . dxp = 0.  r ends at (xp, eta - t k0).
+template <class T, int IP, bool MIXED>
+__device__ bool trace_to_sphere(const DevField& F, const TraceArgs& A, const double* xo, double eta_lo,
+                                const double* th, double chi_s, RayState& r, TanState& ts, SphereHit& hit,
+                                unsigned* err, const LaneCache* lc) {
+  r = ray_start_dir<T>(F, xo, eta_lo, th, A.gravity_on != 0, err);
+  tangent_init_dir(th, r, ts);
+  if (lc) *lc->key = make_int4(-1, 0, 0, 0);
+  for (;;) {
+    bool done;
+    if constexpr (MIXED) {
+      done = tangent_step_mixed<IP>(F, A, r, ts, err, lc);
+    } else {
+      done = tangent_step<T, IP>(F, A, r, ts, err);
+    }
+    if (r.status != MT_RAY_OK) return false;
+    const double d[3] = {r.y[0] - xo[0], r.y[1] - xo[1], r.y[2] - xo[2]};
+    const double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (dd >= chi_s * chi_s) {
+      const double* k = r.y + 5;
+      const double kk = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+      const double b = d[0] * k[0] + d[1] * k[1] + d[2] * k[2];
+      const double t = (b - sqrt(fmax(0.0, b * b - kk * (dd - chi_s * chi_s)))) / kk;
+      for (int q = 0; q < 3; ++q) hit.xp[q] = r.y[q] - t * k[q];
+      const double rp[3] = {hit.xp[0] - xo[0], hit.xp[1] - xo[1], hit.xp[2] - xo[2]};
+      const double rk = rp[0] * k[0] + rp[1] * k[1] + rp[2] * k[2];
+      for (int bb = 0; bb < 2; ++bb) {
+        double u[3];
+        for (int q = 0; q < 3; ++q) u[q] = ts.d[bb][q] - t * ts.d[bb][5 + q];
+        const double dt = (rp[0] * u[0] + rp[1] * u[1] + rp[2] * u[2]) / rk;
+        for (int q = 0; q < 3; ++q) hit.dxp[bb][q] = u[q] - dt * k[q];
+      }
+      for (int q = 0; q < 3; ++q) r.y[q] = hit.xp[q];
+      r.y[3] -= t * r.y[4];
+      r.eta_stop = r.y[3];
+      return true;
+    }
+    if (done) return false;  // the background table ended before the sphere
+  }
+}
+
+// beta_i - beta on the screen of th, and its length.
+__device__ __forceinline__ double finder_residual(const double* xp, const double* xo, double chi_s, const double* beta,
+                                                  const double* e1, const double* e2, double* D) {
+  double v[3];
+  for (int q = 0; q < 3; ++q) v[q] = (xp[q] - xo[q]) / chi_s - beta[q];
+  D[0] = v[0] * e1[0] + v[1] * e1[1] + v[2] * e1[2];
+  D[1] = v[0] * e2[0] + v[1] * e2[1] + v[2] * e2[2];
+  return sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+}
+
+__device__ __forceinline__ void unit_step(const double* th, const double* e1, const double* e2, double a, double b,
+                                          double* out) {
+  double nn = 0.0;
+  for (int q = 0; q < 3; ++q) {
+    out[q] = th[q] + a * e1[q] + b * e2[q];
+    nn += out[q] * out[q];
+  }
+  nn = sqrt(nn);
+  for (int q = 0; q < 3; ++q) out[q] /= nn;
+}
+
+template <class T, int IP, bool MIXED>
+__global__ void __launch_bounds__(kTanBlock) finder_kernel(DevField F, DevCones C, OutPtrs O, FinderPtrs P,
+                                                           TraceArgs A, double tol, int max_newton, int max_grid,
+                                                           unsigned long long* ws) {
+  unsigned* err = (unsigned*)(ws + 1);
+  const unsigned lane = threadIdx.x & 31u;
+  const long long n = A.n_rays;
+  extern __shared__ float4 smem[];
+  LaneCache lc;
+  lc.rec = smem + threadIdx.x;
+  lc.key = (int4*)(smem + 16 * kTanBlock) + threadIdx.x;
+  lc.stride = kTanBlock;
+  lc.loc = (int*)((int4*)(smem + 16 * kTanBlock) + kTanBlock) + threadIdx.x;
+  if (MIXED) *lc.loc = -1;
+  const LaneCache* lcp = MIXED ? &lc : nullptr;
+  long long src = -1;
+  bool exhausted = false;
+  for (;;) {
+    const bool need = (src < 0) && !exhausted;
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(ws, (unsigned long long)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (need) {
+        const long long id = (long long)base + __popc(m & ((1u << lane) - 1u));
+        if (id < n) src = id; else exhausted = true;
+      }
+    }
+    if (!__any_sync(0xffffffffu, src >= 0)) break;
+    if (src < 0) continue;
+    int c = 0;
+    while (c + 1 < C.n && C.begin[c + 1] <= src) ++c;
+    const double* xo = C.obs[c];
+    double beta[3] = {P.src[src] - xo[0], P.src[n + src] - xo[1], P.src[2 * n + src] - xo[2]};
+    const double chi_s = sqrt(beta[0] * beta[0] + beta[1] * beta[1] + beta[2] * beta[2]);
+    for (int q = 0; q < 3; ++q) beta[q] /= chi_s;
+    double th[3] = {beta[0], beta[1], beta[2]};
+    RayState r;
+    TanState ts;
+    SphereHit hit;
+    double e1[3], e2[3], D[2];
+    double res = 1e300;
+    int status = 2, it = 0;
+    bool have = false;  // r, ts, hit hold the trace of th
+    for (; it < max_newton; ++it) {
+      if (!trace_to_sphere<T, IP, MIXED>(F, A, xo, C.eta_stop[c], th, chi_s, r, ts, hit, err, lcp)) {
+        status = 3;
+        break;
+      }
+      have = true;
+      screen_vectors(th, e1, e2);
+      res = finder_residual(hit.xp, xo, chi_s, beta, e1, e2, D);
+      if (res < tol) {
+        status = 0;
+        break;
+      }
+      // A_ab = e_a . dxp_b / chi_s; theta <- theta - A^{-1} D on the screen of theta
+      double a11 = 0, a12 = 0, a21 = 0, a22 = 0;
+      for (int q = 0; q < 3; ++q) {
+        a11 += e1[q] * hit.dxp[0][q];
+        a12 += e1[q] * hit.dxp[1][q];
+        a21 += e2[q] * hit.dxp[0][q];
+        a22 += e2[q] * hit.dxp[1][q];
+      }
+      a11 /= chi_s; a12 /= chi_s; a21 /= chi_s; a22 /= chi_s;
+      const double det = a11 * a22 - a12 * a21;
+      if (!(fabs(det) > 1e-12)) break;  // singular (a caustic): leave it to the grid
+      const double d1 = (a22 * D[0] - a12 * D[1]) / det, d2 = (-a21 * D[0] + a11 * D[1]) / det;
+      double nt[3];
+      unit_step(th, e1, e2, -d1, -d2, nt);
+      for (int q = 0; q < 3; ++q) th[q] = nt[q];
+      have = false;
+    }
+    if (status == 2 && it >= max_newton) it = max_newton;
+    if (status == 2 && res < 1e299) {
+      // shrinking grid around the best direction so far
+      if (!have) {
+        if (trace_to_sphere<T, IP, MIXED>(F, A, xo, C.eta_stop[c], th, chi_s, r, ts, hit, err, lcp)) {
+          screen_vectors(th, e1, e2);
+          res = finder_residual(hit.xp, xo, chi_s, beta, e1, e2, D);
+        }
+      }
+      double sp = 2.0 * res;
+      for (int g = 0; g < max_grid && status == 2; ++g) {
+        screen_vectors(th, e1, e2);
+        double best[3] = {th[0], th[1], th[2]};
+        double bres = res;
+        for (int gi = -2; gi <= 2; ++gi)
+          for (int gj = -2; gj <= 2; ++gj) {
+            if (gi == 0 && gj == 0) continue;
+            double cand[3];
+            unit_step(th, e1, e2, gi * sp, gj * sp, cand);
+            if (!trace_to_sphere<T, IP, MIXED>(F, A, xo, C.eta_stop[c], cand, chi_s, r, ts, hit, err, lcp)) continue;
+            double ce1[3], ce2[3], cD[2];
+            screen_vectors(cand, ce1, ce2);
+            const double cr = finder_residual(hit.xp, xo, chi_s, beta, ce1, ce2, cD);
+            if (cr < bres) {
+              bres = cr;
+              for (int q = 0; q < 3; ++q) best[q] = cand[q];
+            }
+          }
+        for (int q = 0; q < 3; ++q) th[q] = best[q];
+        res = bres;
+        sp *= 0.5;
+        ++it;
+        if (res < tol) status = 1;
+      }
+      have = false;
+    }
+    if (status != 3 && !have) {
+      if (trace_to_sphere<T, IP, MIXED>(F, A, xo, C.eta_stop[c], th, chi_s, r, ts, hit, err, lcp)) {
+        screen_vectors(th, e1, e2);
+        res = finder_residual(hit.xp, xo, chi_s, beta, e1, e2, D);
+        have = true;
+      } else {
+        status = 3;
+      }
+    }
+    if (have) {
+      ray_finish<T>(F, A, r, src, n, O, err);
+      if (P.jac) {
+        double a[4] = {0, 0, 0, 0};
+        for (int q = 0; q < 3; ++q) {
+          a[0] += e1[q] * hit.dxp[0][q];
+          a[1] += e1[q] * hit.dxp[1][q];
+          a[2] += e2[q] * hit.dxp[0][q];
+          a[3] += e2[q] * hit.dxp[1][q];
+        }
+        for (int q = 0; q < 4; ++q) P.jac[q * n + src] = a[q] / chi_s;
+      }
+    }
+    for (int q = 0; q < 3; ++q) P.theta[q * n + src] = th[q];
+    if (P.resid) P.resid[src] = res;
+    if (P.iters) P.iters[src] = it + 1;
+    P.status[src] = status;
+    src = -1;
+  }
+}
+
+template <class T, int IP, bool MIXED>
+void launch_finder_t(const mt_octree* tree, const DevCones& C, const OutPtrs& O, const FinderPtrs& P,
+                     const TraceArgs& A, double tol, int max_newton, int max_grid, cudaStream_t stream) {
+  static int bps = -1;
+  const size_t sm = MIXED ? kTanMixedSmem : 0;
+  if (bps < 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, finder_kernel<T, IP, MIXED>, kTanBlock, sm) !=
+            cudaSuccess ||
+        b < 1)
+      b = 1;
+    bps = b;
+  }
+  finder_kernel<T, IP, MIXED><<<tree->num_sms * bps, kTanBlock, sm, stream>>>(launch_field(tree, A), C, O, P, A, tol,
+                                                                              max_newton, max_grid, tree->ws);
+}
+
+template <int IP>
+void launch_finder_scheme(const mt_octree* tree, const DevCones& C, const OutPtrs& O, const FinderPtrs& P,
+                          const TraceArgs& A, double tol, int max_newton, int max_grid, cudaStream_t stream) {
+  if (tree->precision == MT_FIELD_FP64) {
+    launch_finder_t<double, IP, false>(tree, C, O, P, A, tol, max_newton, max_grid, stream);
+  } else {
+    launch_finder_t<float, IP, true>(tree, C, O, P, A, tol, max_newton, max_grid, stream);
+  }
+}
+
 }  // namespace
 
 // Enqueue the tangent kernel (called by mt_trace_rays_adjoint).
@@ -514,4 +773,52 @@ cudaError_t launch_tangent(const mt_octree* tree, const DevCones& C, const doubl
   return cudaGetLastError();
 }
 
+// Enqueue the geodesic finder (called by mt_find_geodesics).
+void launch_finder(const mt_octree* tree, const DevCones& C, const OutPtrs& O, const FinderPtrs& P, const TraceArgs& A,
+                   double tol, int max_newton, int max_grid, cudaStream_t stream) {
+  switch (A.interp) {
+    case MT_INTERP_NGP: launch_finder_scheme<MT_INTERP_NGP>(tree, C, O, P, A, tol, max_newton, max_grid, stream); break;
+    case MT_INTERP_TSC: launch_finder_scheme<MT_INTERP_TSC>(tree, C, O, P, A, tol, max_newton, max_grid, stream); break;
+    default: launch_finder_scheme<MT_INTERP_CIC>(tree, C, O, P, A, tol, max_newton, max_grid, stream); break;
+  }
+}
+
 }  // namespace mt
+
+using namespace mt;
+
+extern "C" mt_status mt_find_geodesics(const mt_octree* tree, const mt_trace_params* params, const double* src,
+                                       int64_t n_src, double tol, int32_t max_newton, int32_t max_grid,
+                                       const mt_ray_out* out, double* theta, double* jac, double* resid,
+                                       int32_t* iters, int32_t* status, void* stream_) {
+  if (!tree || !out) return MT_ERR_INVALID_ARG;
+  mt_status st = check_trace_params(params, n_src);
+  if (st != MT_OK) return st;
+  if (!(tol > 0.0) || max_newton < 1 || max_newton > 100 || max_grid < 0 || max_grid > 64) return MT_ERR_INVALID_ARG;
+  if (n_src > 0 && (!src || !theta || !status)) return MT_ERR_INVALID_ARG;
+  if (n_src == 0) return MT_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != tree->device && cudaSetDevice(tree->device) != cudaSuccess) return MT_ERR_CUDA;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  DevCones C;
+  fill_cones(tree, params, &C);
+  for (int c = 0; c < C.n; ++c) C.eta_stop[c] = tree->bg_host[0];  // the sphere stops the rays, not eta
+  OutPtrs O = {out->x, out->k, out->eta, out->lambda, out->chi, out->path, out->z0, out->z1, out->z4, out->z5,
+               out->d_a, out->d_l, out->phi_o, out->phi_s, out->isw, out->n_steps, out->level, out->status, out->xi};
+  TraceArgs A;
+  A.steps_per_cell = params->steps_per_cell;
+  A.interp = params->interp;
+  A.pad = 0;
+  A.gravity_on = params->gravity_on ? 1 : 0;
+  A.max_steps = params->max_steps;
+  A.n_rays = n_src;
+  FinderPtrs P = {src, theta, jac, resid, iters, status};
+  cudaError_t e = cudaMemsetAsync(tree->ws, 0, sizeof(unsigned long long), stream);
+  if (e == cudaSuccess) {
+    launch_finder(tree, C, O, P, A, tol, max_newton, max_grid, stream);
+    e = cudaGetLastError();
+  }
+  if (prev >= 0 && prev != tree->device) cudaSetDevice(prev);
+  return e == cudaSuccess ? MT_OK : MT_ERR_CUDA;
+}
