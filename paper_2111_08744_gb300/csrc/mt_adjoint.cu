@@ -33,10 +33,44 @@ struct RecBar {
   double* lv[kMaxLevels + 1];  // [count][S][4] cotangent buffers per level (NULL: skip the level)
 };
 
-// Scatter cotangents of (grad phi, phi_eta, phi) at (x, eta) onto the CIC records used there.
+// Per-lane accumulator of record cotangents in shared memory: the 8 CIC records of both
+// bracketing slices of the last neighbourhood a stage scattered to (acc[(8 c + 4 slice + q) *
+// stride]), their rows and key (level << 8 | slice, i0).  Consecutive stages of a ray mostly land
+// in the same neighbourhood, so the FP64 atomics into the record gradients are issued only when it
+// changes (and at the end of the ray) instead of at every stage.
+struct ScatterCache {
+  double* acc;
+  unsigned* rows;
+  int4* key;   // x = -1: empty
+  int stride;
+};
+
+// Add the accumulated cotangents into the record gradients and empty the accumulator.
+__device__ __noinline__ void scatter_flush(const DevField& F, const RecBar& R, const ScatterCache& sc) {
+  const int4 k = *sc.key;
+  if (k.x < 0) return;
+  const int l = k.x >> 8, s = k.x & 255;
+  double* base = R.lv[l];
+  const int ns = F.S > 1 ? 2 : 1;
+  for (int c = 0; c < 8; ++c) {
+    const unsigned row = sc.rows[c * sc.stride];
+    for (int sl = 0; sl < ns; ++sl) {
+      double* r = base + ((size_t)row * F.S + s + sl) * 4;
+      for (int q = 0; q < 4; ++q) {
+        double* a = sc.acc + (8 * c + 4 * sl + q) * sc.stride;
+        if (*a != 0.0) atomicAdd(r + q, *a);
+        *a = 0.0;
+      }
+    }
+  }
+  *sc.key = make_int4(-1, 0, 0, 0);
+}
+
+// Scatter cotangents of (grad phi, phi_eta, phi) at (x, eta) onto the CIC records used there
+// (through the lane's accumulator when sc is non-null).
 template <class T>
 __device__ void scatter_cotangent(const DevField& F, const double* x, double eta, const double* gbar, double pebar,
-                                  double phibar, const RecBar& R, unsigned* err) {
+                                  double phibar, const RecBar& R, unsigned* err, const ScatterCache* cache = nullptr) {
   double u[3];
   if (!coarse_coords<T>(F, x, u)) return;
   const int lfin = locate_level(F, u, err);
@@ -52,10 +86,18 @@ __device__ void scatter_cotangent(const DevField& F, const double* x, double eta
       i0[d] = (long long)fl;
       f[d] = U - fl;
     }
+    const int4 key = make_int4((l << 8) | s, (int)i0[0], (int)i0[1], (int)i0[2]);
+    const bool hit = cache && cache->key->x == key.x && cache->key->y == key.y && cache->key->z == key.z &&
+                     cache->key->w == key.w;
     unsigned rows[8];
-    if (!cic_rows(F, l, i0, rows, err)) continue;
+    if (!hit && !cic_rows(F, l, i0, rows, err)) continue;
     double* base = R.lv[l];
     if (!base) return;
+    if (cache && !hit) {
+      scatter_flush(F, R, *cache);
+      for (int c = 0; c < 8; ++c) cache->rows[c * cache->stride] = rows[c];
+      *cache->key = key;
+    }
     double a0[4], a1[4];  // per-slice cotangent of (phi, g0, g1, g2) before the CIC weight
     if (F.S == 1) {
       a0[0] = phibar;
@@ -76,6 +118,12 @@ __device__ void scatter_cotangent(const DevField& F, const double* x, double eta
       const double wz = (c & 4) ? f[2] : 1.0 - f[2];
       const double w = wx * wy * wz;
       if (w == 0.0) continue;
+      if (cache) {
+        for (int q = 0; q < 4; ++q) cache->acc[(8 * c + q) * cache->stride] += w * a0[q];
+        if (F.S > 1)
+          for (int q = 0; q < 4; ++q) cache->acc[(8 * c + 4 + q) * cache->stride] += w * a1[q];
+        continue;
+      }
       double* r0 = base + ((size_t)rows[c] * F.S + s) * 4;
       for (int q = 0; q < 4; ++q)
         if (a0[q] != 0.0) atomicAdd(r0 + q, w * a0[q]);
@@ -93,7 +141,7 @@ __device__ void scatter_cotangent(const DevField& F, const double* x, double eta
 // cotangents of the interpolated field at y onto the records.
 template <class T>
 __device__ bool stage_adjoint(const DevField& F, bool grav, const double* y, const double* w, double* ybar,
-                              const RecBar& R, unsigned* err) {
+                              const RecBar& R, unsigned* err, const ScatterCache* sc) {
   double H, dH;
   bg_eval_d(F, y[3], &H, &dH);
   const double k0 = y[4], k[3] = {y[5], y[6], y[7]};
@@ -138,7 +186,7 @@ __device__ bool stage_adjoint(const DevField& F, bool grav, const double* y, con
   }
   for (int i = 0; i < 3; ++i) tb[3] += fd.ge[i] * dgbar[i];
   for (int i = 0; i < 8; ++i) ybar[i] += tb[i];
-  if (grav) scatter_cotangent<T>(F, y, y[3], dgbar, dpebar, 0.0, R, err);
+  if (grav) scatter_cotangent<T>(F, y, y[3], dgbar, dpebar, 0.0, R, err, sc);
   return true;
 }
 
@@ -166,6 +214,14 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(DevField F, DevCones
   const long long n = A.n_rays;
   const bool grav = A.gravity_on != 0;
   double ys[kMaxSegment][8];
+  extern __shared__ double adj_smem[];
+  ScatterCache sc;
+  sc.stride = kAdjBlock;
+  sc.acc = adj_smem + threadIdx.x;
+  sc.rows = (unsigned*)(adj_smem + 64 * kAdjBlock) + threadIdx.x;
+  sc.key = (int4*)((unsigned*)(adj_smem + 64 * kAdjBlock) + 8 * kAdjBlock) + threadIdx.x;
+  for (int j = 0; j < 64; ++j) sc.acc[j * sc.stride] = 0.0;
+  *sc.key = make_int4(-1, 0, 0, 0);
   long long ray = -1;
   bool exhausted = false;
   for (;;) {
@@ -264,7 +320,7 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(DevField F, DevCones
           double Yb[8];
           // stage 4 at Y4 = y + h K3
           for (int i = 0; i < 8; ++i) Yb[i] = 0.0;
-          stage_adjoint<T>(F, grav, Y4, kb4, Yb, R, err);
+          stage_adjoint<T>(F, grav, Y4, kb4, Yb, R, err, &sc);
           for (int i = 0; i < 8; ++i) {
             nyb[i] += Yb[i];
             kb3[i] += h * Yb[i];
@@ -272,7 +328,7 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(DevField F, DevCones
           }
           // stage 3 at Y3 = y + h/2 K2
           for (int i = 0; i < 8; ++i) Yb[i] = 0.0;
-          stage_adjoint<T>(F, grav, Y3, kb3, Yb, R, err);
+          stage_adjoint<T>(F, grav, Y3, kb3, Yb, R, err, &sc);
           for (int i = 0; i < 8; ++i) {
             nyb[i] += Yb[i];
             kb2[i] += h2 * Yb[i];
@@ -280,7 +336,7 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(DevField F, DevCones
           }
           // stage 2 at Y2 = y + h/2 K1
           for (int i = 0; i < 8; ++i) Yb[i] = 0.0;
-          stage_adjoint<T>(F, grav, Y2, kb2, Yb, R, err);
+          stage_adjoint<T>(F, grav, Y2, kb2, Yb, R, err, &sc);
           for (int i = 0; i < 8; ++i) {
             nyb[i] += Yb[i];
             kb1[i] += h2 * Yb[i];
@@ -288,7 +344,7 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(DevField F, DevCones
           }
           // stage 1 at y
           for (int i = 0; i < 8; ++i) Yb[i] = 0.0;
-          stage_adjoint<T>(F, grav, y10, kb1, Yb, R, err);
+          stage_adjoint<T>(F, grav, y10, kb1, Yb, R, err, &sc);
           for (int i = 0; i < 8; ++i) nyb[i] += Yb[i];
           // step size: h = dx_l / (N |k0|), or (eta_stop - eta) / k0 on the last step
           const double k0 = y[4];
@@ -305,9 +361,10 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(DevField F, DevCones
                                   (1.0 - 2.0 * po) * (1.0 - 2.0 * po));
         const double phib = (yb[5] * nd[0] + yb[6] * nd[1] + yb[7] * nd[2]) * dkn;
         const double zero[3] = {0.0, 0.0, 0.0};
-        scatter_cotangent<T>(F, r.xo, F.eta_o, zero, 0.0, phib, R, err);
+        scatter_cotangent<T>(F, r.xo, F.eta_o, zero, 0.0, phib, R, err, &sc);
       }
     }
+    scatter_flush(F, R, sc);
     ray = -1;
   }
 }
@@ -352,10 +409,11 @@ cudaError_t launch_adjoint(const mt_octree* tree, const DevCones& C, const doubl
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(tree->ws, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
+  const size_t smem = (size_t)kAdjBlock * (64 * sizeof(double) + 8 * sizeof(unsigned) + sizeof(int4));
   int bps = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, adjoint_kernel<T>, kAdjBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, adjoint_kernel<T>, kAdjBlock, smem);
   if (bps < 1) bps = 1;
-  adjoint_kernel<T><<<tree->num_sms * bps, kAdjBlock, 0, stream>>>(launch_field(tree, A), C, dirs, O, A, dL_dxi, R, *d_ck_out,
+  adjoint_kernel<T><<<tree->num_sms * bps, kAdjBlock, smem, stream>>>(launch_field(tree, A), C, dirs, O, A, dL_dxi, R, *d_ck_out,
                                                                     *d_off_out, seg_len, tree->ws);
   return cudaGetLastError();
 }
