@@ -66,8 +66,9 @@ struct LaneCache {
   float4* rec;   // rec[j * stride] for j = 0..15 (corner-major, lanes interleaved: no bank conflicts)
   int4* key;     // (level << 8 | slice, i0x, i0y, i0z); level -1: empty
   int stride;
-  int* loc;      // last coarse cell looked up, packed x | y << 10 | z << 20, bit 30: refined; -1: empty
-                 // (a property of the field, valid across rays; used when N_0 <= 1024; may be null)
+  int4* loc;     // last locate answer: the cell (x, y, z) of level w that contains the point, w the
+                 // finest level there (w = -1: empty); a property of the field, valid across rays;
+                 // may be null
 };
 
 // CIC at level l (FP32) from finest-level integer coordinates; v as in cic_gather.  With
@@ -198,31 +199,30 @@ __device__ __forceinline__ bool interp_int(const DevField& F, int l, const int* 
 __device__ __forceinline__ int locate_level_int(const DevField& F, const int* ic, unsigned* err,
                                                 const LaneCache* lc = nullptr) {
   if (F.L == 0) return 0;
-  const unsigned sh0 = (unsigned)F.L;
-  const unsigned cx = (unsigned)ic[0] >> sh0, cy = (unsigned)ic[1] >> sh0, cz = (unsigned)ic[2] >> sh0;
-  if (lc && lc->loc && F.nc <= 1024) {
-    // consecutive stages of a ray nearly always stay in one coarse cell: reuse its refinement bit
-    const int packed = (int)(cx | (cy << 10) | (cz << 20));
-    const int old = *lc->loc;
-    bool refined;
-    if (old >= 0 && (old & 0x3fffffff) == packed) {
-      refined = (old >> 30) != 0;
-    } else {
-      const unsigned long long crow = morton(cx, cy, cz);
-      refined = ((__ldg(&F.refbits[crow >> 5]) >> (crow & 31ull)) & 1u) != 0;
-      *lc->loc = packed | (refined ? (1 << 30) : 0);
+  if (lc && lc->loc) {
+    // the answer depends only on the cell of the level found (it exists and, refined levels holding
+    // whole octets, has no children): reuse it while the point stays in that cell
+    const int4 c = *lc->loc;
+    if (c.w >= 0) {
+      const int sh = F.L - c.w;
+      if ((ic[0] >> sh) == c.x && (ic[1] >> sh) == c.y && (ic[2] >> sh) == c.z) return c.w;
     }
-    if (!refined) return 0;
-  } else {
-    const unsigned long long crow = morton(cx, cy, cz);
-    if (!((__ldg(&F.refbits[crow >> 5]) >> (crow & 31ull)) & 1u)) return 0;
   }
-  int lf = 1;
-  for (int l = 2; l <= F.L; ++l) {
-    const int sh = F.L - l + 1;
-    const unsigned long long pk = morton((unsigned)ic[0] >> sh, (unsigned)ic[1] >> sh, (unsigned)ic[2] >> sh);
-    if (hash_find(F.hash[l], pk, err) < 0) break;
-    lf = l;
+  const unsigned sh0 = (unsigned)F.L;
+  const unsigned long long crow = morton((unsigned)ic[0] >> sh0, (unsigned)ic[1] >> sh0, (unsigned)ic[2] >> sh0);
+  int lf = 0;
+  if ((__ldg(&F.refbits[crow >> 5]) >> (crow & 31ull)) & 1u) {
+    lf = 1;
+    for (int l = 2; l <= F.L; ++l) {
+      const int sh = F.L - l + 1;
+      const unsigned long long pk = morton((unsigned)ic[0] >> sh, (unsigned)ic[1] >> sh, (unsigned)ic[2] >> sh);
+      if (hash_find(F.hash[l], pk, err) < 0) break;
+      lf = l;
+    }
+  }
+  if (lc && lc->loc) {
+    const int sh = F.L - lf;
+    *lc->loc = make_int4(ic[0] >> sh, ic[1] >> sh, ic[2] >> sh, lf);
   }
   return lf;
 }

@@ -421,8 +421,8 @@ __global__ void __launch_bounds__(kTanBlock) tangent_kernel_mixed(DevField F, De
   lc.rec = smem + threadIdx.x;
   lc.key = (int4*)(smem + 16 * kTanBlock) + threadIdx.x;
   lc.stride = kTanBlock;
-  lc.loc = (int*)((int4*)(smem + 16 * kTanBlock) + kTanBlock) + threadIdx.x;
-  *lc.loc = -1;
+  lc.loc = (int4*)(smem + 16 * kTanBlock) + kTanBlock + threadIdx.x;
+  *lc.loc = make_int4(0, 0, 0, -1);
   RayState r;
   TanState ts;
   long long ray = -1;
@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(kTanBlock) tangent_kernel_mixed(DevField F, De
   }
 }
 
-constexpr size_t kTanMixedSmem = (size_t)kTanBlock * (16 * sizeof(float4) + sizeof(int4) + sizeof(int));
+constexpr size_t kTanMixedSmem = (size_t)kTanBlock * (16 * sizeof(float4) + 2 * sizeof(int4));
 
 template <int IP>
 int tangent_mixed_blocks_per_sm() {
@@ -602,8 +602,8 @@ __global__ void __launch_bounds__(kTanBlock) finder_kernel(DevField F, DevCones 
   lc.rec = smem + threadIdx.x;
   lc.key = (int4*)(smem + 16 * kTanBlock) + threadIdx.x;
   lc.stride = kTanBlock;
-  lc.loc = (int*)((int4*)(smem + 16 * kTanBlock) + kTanBlock) + threadIdx.x;
-  if (MIXED) *lc.loc = -1;
+  lc.loc = (int4*)(smem + 16 * kTanBlock) + kTanBlock + threadIdx.x;
+  if (MIXED) *lc.loc = make_int4(0, 0, 0, -1);
   const LaneCache* lcp = MIXED ? &lc : nullptr;
   long long src = -1;
   bool exhausted = false;

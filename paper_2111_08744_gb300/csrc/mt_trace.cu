@@ -45,8 +45,8 @@ __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCone
   lc.rec = smem + threadIdx.x;
   lc.key = (int4*)(smem + 16 * BS) + threadIdx.x;
   lc.stride = BS;
-  lc.loc = (int*)((int4*)(smem + 16 * BS) + BS) + threadIdx.x;
-  if (sizeof(T) == 4) *lc.loc = -1;
+  lc.loc = (int4*)(smem + 16 * BS) + BS + threadIdx.x;
+  if (sizeof(T) == 4) *lc.loc = make_int4(0, 0, 0, -1);
   const LaneCache* lcp = sizeof(T) == 4 ? &lc : nullptr;
   RayState r;
   long long ray = -1;
@@ -97,10 +97,10 @@ __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCone
 }
 
 // Dynamic shared memory of trace_kernel<T, BS>: the mixed path's per-thread neighbourhood cache and
-// coarse refinement bit (276 B per thread).
+// last locate answer (288 B per thread).
 template <class T, int BS>
 constexpr size_t trace_smem() {
-  return sizeof(T) == 4 ? (size_t)BS * (16 * sizeof(float4) + sizeof(int4) + sizeof(int)) : 0;
+  return sizeof(T) == 4 ? (size_t)BS * (16 * sizeof(float4) + 2 * sizeof(int4)) : 0;
 }
 
 template <class T, int BS, int IP>
