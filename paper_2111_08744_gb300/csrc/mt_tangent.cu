@@ -405,6 +405,10 @@ __global__ void __launch_bounds__(kTanBlock) tangent_kernel(DevField F, DevCones
   }
 }
 
+// Ray ids a warp of the mixed tangent kernel claims at a time (sky neighbours share cache lines,
+// as in trace_kernel).
+constexpr int kTanChunk = 32;
+
 // FP32 fields: the mixed tangent step, with each ray's CIC neighbourhood staged in shared
 // memory as in trace_kernel.
 template <int IP>
@@ -427,16 +431,31 @@ __global__ void __launch_bounds__(kTanBlock) tangent_kernel_mixed(DevField F, De
   TanState ts;
   long long ray = -1;
   bool exhausted = false;
+  unsigned long long pool = 0;  // next id of this warp's chunk of kTanChunk consecutive ids (warp-uniform)
+  int pool_left = 0;
   for (;;) {
     const bool need = (ray < 0) && !exhausted;
     const unsigned m = __ballot_sync(0xffffffffu, need);
     if (m) {
       const int leader = __ffs(m) - 1;
-      unsigned long long base = 0;
-      if ((int)lane == leader) base = atomicAdd(ws, (unsigned long long)__popc(m));
-      base = __shfl_sync(0xffffffffu, base, leader);
+      const int k = __popc(m);
+      const int from_pool = k < pool_left ? k : pool_left;
+      unsigned long long fresh = 0;
+      if (k > from_pool) {
+        if ((int)lane == leader) fresh = atomicAdd(ws, (unsigned long long)kTanChunk);
+        fresh = __shfl_sync(0xffffffffu, fresh, leader);
+      }
+      const int rank = __popc(m & ((1u << lane) - 1u));
+      const unsigned long long pick = rank < from_pool ? pool + rank : fresh + (rank - from_pool);
+      if (k > from_pool) {
+        pool = fresh + (k - from_pool);
+        pool_left = kTanChunk - (k - from_pool);
+      } else {
+        pool += k;
+        pool_left -= k;
+      }
       if (need) {
-        const long long id = (long long)base + __popc(m & ((1u << lane) - 1u));
+        const long long id = (long long)pick;
         if (id < n) {
           ray = id;
           int c = 0;
