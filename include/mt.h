@@ -285,7 +285,7 @@ mt_status mt_trace_beams(const mt_octree* tree, const mt_trace_params* params, c
  * around the best direction, halving its spacing each round.  Rays advance as in the trace calls;
  * the background table's first node bounds them.  Outputs (device, length N): theta [3][N];
  * jac [4][N] (A11, A12, A21, A22 at the solution, or NULL); resid [N] (|beta_i - beta|, or NULL);
- * iters [N] (traces per source, or NULL); status [N]: 0 converged by Newton, 1 by the grid,
+ * iters [N] (Newton iterations + grid rounds + 1, or NULL); status [N]: 0 converged by Newton, 1 by the grid,
  * 2 not converged (theta is the best found), 3 the ray failed; `out` receives the solution ray's
  * outputs at the sphere (x on it; z0..z5, phi_s, isw at that point).  Asynchronous.
  * Errors: as mt_trace_rays's parameter checks; MT_ERR_INVALID_ARG for tol <= 0, out-of-range

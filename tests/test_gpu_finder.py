@@ -26,13 +26,14 @@ def _sources(w, n, seed, chi_lo=100.0, chi_hi=1000.0):
     return w.observer[0][:, None] + chi * v, chi, v
 
 
-def _find(w, precision, src, tol, gravity_on=True, interp="cic"):
+def _find(w, precision, src, tol, gravity_on=True, interp="cic", max_newton=10, max_grid=20):
     import torch
     from paper_2111_08744_gb300 import binding as B
     tree = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, w.levels, w.bg, precision)
     cap = B.step_cap(w.bg, w.box / w.n_coarse, len(w.levels) - 1, w.steps_per_cell, 3.0)
     p = B.TraceParams(w.observer, [0.0], [0, src.shape[1]], w.steps_per_cell, gravity_on, cap, interp)
-    r = B.find_geodesics(tree, p, torch.from_numpy(np.ascontiguousarray(src)).cuda(), tol=tol)
+    r = B.find_geodesics(tree, p, torch.from_numpy(np.ascontiguousarray(src)).cuda(), tol=tol, max_newton=max_newton,
+                         max_grid=max_grid)
     torch.cuda.synchronize()
     assert tree.device_status() == B.MT_OK
     tree.free()
@@ -85,3 +86,21 @@ def test_fp32_field_mixed_solutions():
     err = np.linalg.norm(beta - v[:, ok], axis=0)
     print("mixed: oracle residual median", np.median(err), "max", err.max())
     assert np.median(err) < 1e-8 and np.mean(err < 1e-6) >= 0.97
+
+
+def test_grid_fallback_reduces_the_residual():
+    """One Newton iteration, then the shrinking grid: each round keeps the best of 25 directions, so
+    the residual never grows and ends far below the first iterate's."""
+    w = amr_small()
+    src, chi, v = _sources(w, 64, 4)
+    one = _find(w, "fp64", src, 1e-14, max_newton=1, max_grid=0)
+    grid = _find(w, "fp64", src, 1e-14, max_newton=1, max_grid=12)
+    assert (grid["fstatus"] != 3).all()
+    assert (grid["resid"] <= one["resid"] * (1 + 1e-12)).all()
+    assert np.median(grid["resid"]) < 0.05 * np.median(one["resid"])
+    # traces: the Newton iterate, one per grid round (a source may converge and stop early), the final one
+    assert (grid["iters"] <= 1 + 12 + 1).all()
+    assert ((grid["iters"] == 1 + 12 + 1) | (grid["fstatus"] == 1)).all()
+    beta, _ = _oracle_beta(w, grid["theta"], chi)
+    # the oracle's map and the GPU's FP64 map differ by ~1e-11 rad
+    np.testing.assert_allclose(np.linalg.norm(beta - v, axis=0), grid["resid"], rtol=1e-3, atol=3e-11)
