@@ -43,7 +43,7 @@ TRACE_KERNEL_SOURCES = ["include/mt.h", "paper_2111_08744_gb300/csrc/mt_internal
                         "paper_2111_08744_gb300/csrc/mt_mixed.cuh", "paper_2111_08744_gb300/csrc/mt_trace_device.cuh",
                         "paper_2111_08744_gb300/csrc/mt_trace.cu"]
 NCU_TRAFFIC = {"bytes_per_launch": 57.97e9 + 0.964e9,
-               "sources_sha256": "fbe6d2598d42a4ae39e72c147fea9203d0fa52667dc76c7c917b890af20a7927"}
+               "sources_sha256": "384ab8f7380c8f8146e507bfd018fd98cf9288790942ac5723797e3c5785c96e"}
 
 
 def trace_kernel_sha256():
