@@ -66,3 +66,13 @@ def test_born_and_full_agree_to_first_order_and_track_finite_beams():
     assert np.corrcoef(k_fin, k_full)[0, 1] > 0.9
     slope = np.polyfit(k_fin, k_full, 1)[0]
     assert 0.5 < slope < 1.2, slope
+
+
+def test_full_sky_mean_convergence_vanishes():
+    """Over the full sky the finite-beam convergence averages to zero within its sampling error
+    (a statement the paper makes about its maps; lensing conserves the total solid angle)."""
+    w = I.config_plain_small()                      # full-sky HEALPix rays, nside 16
+    A = oracle.bundle_jacobian(w, eps=1e-4)
+    kappa = 1 - 0.5 * (A[0] + A[3])
+    assert kappa.std() > 1e-3
+    assert abs(kappa.mean()) < 4 * kappa.std() / np.sqrt(kappa.size)
