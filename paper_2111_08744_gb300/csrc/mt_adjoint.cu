@@ -1,3 +1,4 @@
+// build: fp64
 // Reverse mode: gradient of a loss on the rays' end points with respect to the gridded
 // potential records (every level, slice and component), by the exact adjoint of the
 // discrete ray map (RK4 of Eqs. 2-4 with CIC interpolation and level fallback, Sect. 2.2).

@@ -1,3 +1,4 @@
+// build: precision-split
 // Finite-beam distortion matrix (Sect. 2.3.2, Eqs. 17-21) on the GPU.
 //
 // A beam is a central ray plus four rays at semi-aperture eps around it: directions
@@ -168,8 +169,18 @@ void launch_beams_scheme(const mt_octree* tree, const DevCones& C, const double*
 }
 
 }  // namespace
+
+#ifdef MT_TU_FP64
+// FP64-field instantiations (this translation unit is compiled without FMA contraction).
+void launch_beams_fp64(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O, double* jac,
+                       double* lens, const TraceArgs& A, double tan_eps, int screen, cudaStream_t stream) {
+  launch_beams_scheme<double>(tree, C, dirs, O, jac, lens, A, tan_eps, screen, stream);
+}
+#endif
+
 }  // namespace mt
 
+#ifndef MT_TU_FP64
 using namespace mt;
 
 extern "C" mt_status mt_trace_beams(const mt_octree* tree, const mt_trace_params* params, const double* dirs,
@@ -201,7 +212,7 @@ extern "C" mt_status mt_trace_beams(const mt_octree* tree, const mt_trace_params
   cudaError_t e = cudaMemsetAsync(tree->ws, 0, sizeof(unsigned long long), stream);
   if (e == cudaSuccess) {
     if (tree->precision == MT_FIELD_FP64) {
-      launch_beams_scheme<double>(tree, C, dirs, O, jac, lens, A, tan_eps, screen, stream);
+      launch_beams_fp64(tree, C, dirs, O, jac, lens, A, tan_eps, screen, stream);
     } else {
       launch_beams_scheme<float>(tree, C, dirs, O, jac, lens, A, tan_eps, screen, stream);
     }
@@ -210,3 +221,4 @@ extern "C" mt_status mt_trace_beams(const mt_octree* tree, const mt_trace_params
   if (prev >= 0 && prev != tree->device) cudaSetDevice(prev);
   return e == cudaSuccess ? MT_OK : MT_ERR_CUDA;
 }
+#endif  // MT_TU_FP64

@@ -6,22 +6,18 @@
 
 namespace mt {
 
-// Hermite H(eta) and its derivative dH/deta.
+// Hermite H(eta) and its derivative dH/deta (the interpolant of bg_eval).
 __device__ __forceinline__ void bg_eval_d(const DevField& F, double eta, double* H, double* dH) {
-  double t0 = (eta - F.bg_eta0) * F.bg_inv_deta;
-  double jf = floor(t0);
-  jf = fmin(fmax(jf, 0.0), (double)(F.bg_n - 2));
-  int j = (int)jf;
-  double t = t0 - jf;
-  dvec4 p = ldg4(&F.bg[j]);
-  dvec4 q = ldg4(&F.bg[j + 1]);
-  double d = F.bg_deta;
-  double t2 = t * t, t3 = t2 * t;
+  dvec4 p, q;
+  bg_interval(F, eta, &p, &q);
+  const double d = q.x - p.x;
+  const double t = (eta - p.x) / d;
+  const double t2 = t * t, t3 = t2 * t;
   *H = (2.0 * t3 - 3.0 * t2 + 1.0) * p.z + (t3 - 2.0 * t2 + t) * d * p.w + (-2.0 * t3 + 3.0 * t2) * q.z +
        (t3 - t2) * d * q.w;
   *dH = ((6.0 * t2 - 6.0 * t) * p.z + (3.0 * t2 - 4.0 * t + 1.0) * d * p.w + (-6.0 * t2 + 6.0 * t) * q.z +
-         (3.0 * t2 - 2.0 * t) * d * q.w) *
-        F.bg_inv_deta;
+         (3.0 * t2 - 2.0 * t) * d * q.w) /
+        d;
 }
 
 struct FieldD {

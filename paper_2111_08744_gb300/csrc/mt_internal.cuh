@@ -115,21 +115,39 @@ __device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
 
 // ----------------------------------------------------------------- background (Sect. 2.2 tables)
 
-// Cubic Hermite interpolation of a(eta) (slopes a H) and H(eta) (slopes dH/deta).
-__device__ __forceinline__ void bg_eval(const DevField& F, double eta, double* a, double* H) {
-  double t0 = (eta - F.bg_eta0) * F.bg_inv_deta;
-  double jf = floor(t0);
+// Node interval of the background table holding eta: eta_j <= eta < eta_{j+1}, clamped to the
+// table's first and last intervals.  The uniform spacing gives the guess; a guess one node off (eta
+// within rounding of a node) is corrected against the nodes themselves.  *p, *q: nodes j, j + 1.
+__device__ __forceinline__ int bg_interval(const DevField& F, double eta, dvec4* p, dvec4* q) {
+  double jf = floor((eta - F.bg_eta0) * F.bg_inv_deta);
   jf = fmin(fmax(jf, 0.0), (double)(F.bg_n - 2));
   int j = (int)jf;
-  double t = t0 - jf;
-  dvec4 p = ldg4(&F.bg[j]);
-  dvec4 q = ldg4(&F.bg[j + 1]);
-  double d = F.bg_deta;
-  double t2 = t * t, t3 = t2 * t;
-  double h00 = 2.0 * t3 - 3.0 * t2 + 1.0;
-  double h10 = t3 - 2.0 * t2 + t;
-  double h01 = -2.0 * t3 + 3.0 * t2;
-  double h11 = t3 - t2;
+  *p = ldg4(&F.bg[j]);
+  *q = ldg4(&F.bg[j + 1]);
+  if (j > 0 && eta < p->x) {
+    --j;
+    *q = *p;
+    *p = ldg4(&F.bg[j]);
+  } else if (j < F.bg_n - 2 && !(eta < q->x)) {
+    ++j;
+    *p = *q;
+    *q = ldg4(&F.bg[j + 1]);
+  }
+  return j;
+}
+
+// Cubic Hermite interpolation of a(eta) (slopes a H) and H(eta) (slopes dH/deta) on the node
+// interval holding eta, t = (eta - eta_j) / (eta_{j+1} - eta_j).
+__device__ __forceinline__ void bg_eval(const DevField& F, double eta, double* a, double* H) {
+  dvec4 p, q;
+  bg_interval(F, eta, &p, &q);
+  const double d = q.x - p.x;
+  const double t = (eta - p.x) / d;
+  const double t2 = t * t, t3 = t2 * t;
+  const double h00 = 2.0 * t3 - 3.0 * t2 + 1.0;
+  const double h10 = t3 - 2.0 * t2 + t;
+  const double h01 = -2.0 * t3 + 3.0 * t2;
+  const double h11 = t3 - t2;
   if (a) *a = h00 * p.y + h10 * d * (p.y * p.z) + h01 * q.y + h11 * d * (q.y * q.z);
   if (H) *H = h00 * p.z + h10 * d * p.w + h01 * q.z + h11 * d * q.w;
 }
@@ -487,12 +505,11 @@ __device__ __forceinline__ bool sample_field(const DevField& F, const double* x,
   }
   const double de = F.seta[s + 1] - F.seta[s];
   const T w = (T)((eta - F.seta[s]) / de);
-  const T ide = (T)(1.0 / de);
   *phi = v[0] + w * (v[4] - v[0]);
   g[0] = v[1] + w * (v[5] - v[1]);
   g[1] = v[2] + w * (v[6] - v[2]);
   g[2] = v[3] + w * (v[7] - v[3]);
-  *pe = (v[4] - v[0]) * ide;
+  *pe = (v[4] - v[0]) / (T)de;
   return true;
 }
 

@@ -1,3 +1,4 @@
+// build: precision-split
 // Infinitesimal-beam distortion matrix along the traced rays (Sect. 2.3.1, Eq. 12):
 //   A_ab = delta_ab - 2 int_0^chi_s dchi (chi_s - chi) chi / chi_s  d_a d_b phi,
 // with the Cartesian Hessian of phi from central differences of the interpolated force (Eq. 13,
@@ -171,8 +172,18 @@ void launch_lensing_scheme(const mt_octree* tree, const DevCones& C, const doubl
 }
 
 }  // namespace
+
+#ifdef MT_TU_FP64
+// FP64-field instantiations (this translation unit is compiled without FMA contraction).
+void launch_lensing_fp64(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O, double* jac,
+                         double* lens, const TraceArgs& A, cudaStream_t stream) {
+  launch_lensing_scheme<double>(tree, C, dirs, O, jac, lens, A, stream);
+}
+#endif
+
 }  // namespace mt
 
+#ifndef MT_TU_FP64
 using namespace mt;
 
 extern "C" mt_status mt_trace_rays_lensing(const mt_octree* tree, const mt_trace_params* params, const double* dirs,
@@ -202,7 +213,7 @@ extern "C" mt_status mt_trace_rays_lensing(const mt_octree* tree, const mt_trace
   cudaError_t e = cudaMemsetAsync(tree->ws, 0, sizeof(unsigned long long), stream);
   if (e == cudaSuccess) {
     if (tree->precision == MT_FIELD_FP64) {
-      launch_lensing_scheme<double>(tree, C, dirs, O, jac, lens, A, stream);
+      launch_lensing_fp64(tree, C, dirs, O, jac, lens, A, stream);
     } else {
       launch_lensing_scheme<float>(tree, C, dirs, O, jac, lens, A, stream);
     }
@@ -211,3 +222,4 @@ extern "C" mt_status mt_trace_rays_lensing(const mt_octree* tree, const mt_trace
   if (prev >= 0 && prev != tree->device) cudaSetDevice(prev);
   return e == cudaSuccess ? MT_OK : MT_ERR_CUDA;
 }
+#endif  // MT_TU_FP64

@@ -103,19 +103,25 @@ mt_status from_cuda(cudaError_t e) {
 }  // namespace
 
 void host_bg_eval(const double* tab, int n, double eta, double* a, double* H) {
+  // node interval holding eta (eta_j <= eta < eta_{j+1}, clamped), as the device's bg_interval
   const double e0 = tab[0];
   const double de = (tab[4 * (n - 1)] - e0) / (double)(n - 1);
-  double t0 = (eta - e0) / de;
-  double jf = std::floor(t0);
+  double jf = std::floor((eta - e0) / de);
   jf = std::fmin(std::fmax(jf, 0.0), (double)(n - 2));
   int j = (int)jf;
-  double t = t0 - jf;
+  if (j > 0 && eta < tab[4 * j]) {
+    --j;
+  } else if (j < n - 2 && !(eta < tab[4 * (j + 1)])) {
+    ++j;
+  }
   const double* p = tab + 4 * j;
   const double* q = p + 4;
+  const double d = q[0] - p[0];
+  const double t = (eta - p[0]) / d;
   double t2 = t * t, t3 = t2 * t;
   double h00 = 2.0 * t3 - 3.0 * t2 + 1.0, h10 = t3 - 2.0 * t2 + t, h01 = -2.0 * t3 + 3.0 * t2, h11 = t3 - t2;
-  if (a) *a = h00 * p[1] + h10 * de * (p[1] * p[2]) + h01 * q[1] + h11 * de * (q[1] * q[2]);
-  if (H) *H = h00 * p[2] + h10 * de * p[3] + h01 * q[2] + h11 * de * q[3];
+  if (a) *a = h00 * p[1] + h10 * d * (p[1] * p[2]) + h01 * q[1] + h11 * d * (q[1] * q[2]);
+  if (H) *H = h00 * p[2] + h10 * d * p[3] + h01 * q[2] + h11 * d * q[3];
 }
 
 // eta at which a(eta) = 1/(1+z): bisection on the (monotone) background interpolant.

@@ -1,3 +1,4 @@
+// build: fp64
 // Pull-back of record cotangents to the coarse potential (the transpose of the field model
 // documented at mt_pullback_coarse_phi in mt.h).
 //

@@ -1,3 +1,4 @@
+// build: precision-split
 // Distortion matrix by forward-mode tangents of the discrete ray map (Sect. 2.3).
 //
 // For each ray two tangent vectors dY_b = (dx[3], deta, dk0, dk[3]) are carried alongside
@@ -109,9 +110,9 @@ __device__ bool tangent_step(const DevField& F, const TraceArgs& A, RayState& r,
     for (int b = 0; b < 2; ++b) dh[b] = -h * ts.d[b][4] / k0;
   }
   const double h2 = 0.5 * h, h3 = h / 3.0, h6 = h / 6.0;
-  // stage 1 -> 2
+  // stage 1 -> 2 (the state as ray_step_fp64: y + (h/6) (K1 + 2 K2 + 2 K3 + K4), summed left to right)
   for (int i = 0; i < 10; ++i) {
-    acc[i] = r.y[i] + h6 * K[i];
+    acc[i] = K[i];
     t[i] = r.y[i] + h2 * K[i];
   }
   for (int b = 0; b < 2; ++b)
@@ -124,7 +125,7 @@ __device__ bool tangent_step(const DevField& F, const TraceArgs& A, RayState& r,
     return true;
   }
   for (int i = 0; i < 10; ++i) {
-    acc[i] += h3 * K[i];
+    acc[i] = acc[i] + 2.0 * K[i];
     t[i] = r.y[i] + h2 * K[i];
   }
   for (int b = 0; b < 2; ++b)
@@ -137,7 +138,7 @@ __device__ bool tangent_step(const DevField& F, const TraceArgs& A, RayState& r,
     return true;
   }
   for (int i = 0; i < 10; ++i) {
-    acc[i] += h3 * K[i];
+    acc[i] = acc[i] + 2.0 * K[i];
     t[i] = r.y[i] + h * K[i];
   }
   for (int b = 0; b < 2; ++b)
@@ -151,7 +152,7 @@ __device__ bool tangent_step(const DevField& F, const TraceArgs& A, RayState& r,
   }
   bool finite = true;
   for (int i = 0; i < 10; ++i) {
-    r.y[i] = acc[i] + h6 * K[i];
+    r.y[i] = r.y[i] + h6 * (acc[i] + K[i]);
     finite = finite && isfinite(r.y[i]);
   }
   for (int b = 0; b < 2; ++b)
@@ -509,17 +510,17 @@ int tangent_blocks_per_sm() {
   return cached;
 }
 
-// FP64 field: FP64 tangent step; FP32 field: the mixed tangent step.
+// FP64 field: FP64 tangent step (FP64 translation unit); FP32 field: the mixed tangent step.
 template <int IP>
 void launch_tangent_scheme(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O,
                            double* jac, double* lens, const TraceArgs& A, cudaStream_t stream) {
-  if (tree->precision == MT_FIELD_FP64) {
-    tangent_kernel<double, IP><<<tree->num_sms * tangent_blocks_per_sm<IP>(), kTanBlock, 0, stream>>>(
-        launch_field(tree, A), C, dirs, O, jac, lens, A, tree->ws);
-  } else {
-    tangent_kernel_mixed<IP><<<tree->num_sms * tangent_mixed_blocks_per_sm<IP>(), kTanBlock, kTanMixedSmem, stream>>>(
-        launch_field(tree, A), C, dirs, O, jac, lens, A, tree->ws);
-  }
+#ifdef MT_TU_FP64
+  tangent_kernel<double, IP><<<tree->num_sms * tangent_blocks_per_sm<IP>(), kTanBlock, 0, stream>>>(
+      launch_field(tree, A), C, dirs, O, jac, lens, A, tree->ws);
+#else
+  tangent_kernel_mixed<IP><<<tree->num_sms * tangent_mixed_blocks_per_sm<IP>(), kTanBlock, kTanMixedSmem, stream>>>(
+      launch_field(tree, A), C, dirs, O, jac, lens, A, tree->ws);
+#endif
 }
 
 // ----------------------------------------------------------------------------- geodesic finder
@@ -531,6 +532,9 @@ void launch_tangent_scheme(const mt_octree* tree, const DevCones& C, const doubl
 // onto the sphere along k) from the first iteration; after max_newton iterations a shrinking 5 x 5
 // grid of directions around the best one.  Status: 0 Newton converged, 1 grid converged, 2 not
 // converged, 3 the ray failed (left the domain, step cap, or the background table ended first).
+}  // namespace
+
+// (outside the unnamed namespace: the FP64 translation unit's launch takes it too)
 struct FinderPtrs {
   const double* src;
   double* theta;
@@ -539,6 +543,8 @@ struct FinderPtrs {
   int32_t* iters;
   int32_t* status;
 };
+
+namespace {
 
 struct SphereHit {
   double xp[3];       // end point on the sphere
@@ -770,31 +776,38 @@ void launch_finder_t(const mt_octree* tree, const DevCones& C, const OutPtrs& O,
 template <int IP>
 void launch_finder_scheme(const mt_octree* tree, const DevCones& C, const OutPtrs& O, const FinderPtrs& P,
                           const TraceArgs& A, double tol, int max_newton, int max_grid, cudaStream_t stream) {
-  if (tree->precision == MT_FIELD_FP64) {
-    launch_finder_t<double, IP, false>(tree, C, O, P, A, tol, max_newton, max_grid, stream);
-  } else {
-    launch_finder_t<float, IP, true>(tree, C, O, P, A, tol, max_newton, max_grid, stream);
-  }
+#ifdef MT_TU_FP64
+  launch_finder_t<double, IP, false>(tree, C, O, P, A, tol, max_newton, max_grid, stream);
+#else
+  launch_finder_t<float, IP, true>(tree, C, O, P, A, tol, max_newton, max_grid, stream);
+#endif
 }
 
 }  // namespace
 
-// Enqueue the tangent kernel (called by mt_trace_rays_adjoint).
-cudaError_t launch_tangent(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O, double* jac,
-                           double* lens, const TraceArgs& A, cudaStream_t stream) {
-  cudaError_t e = cudaMemsetAsync(tree->ws, 0, sizeof(unsigned long long), stream);
-  if (e != cudaSuccess) return e;
+// The tangent and finder kernels of this translation unit's field precision: FP64 fields in the
+// unit compiled with MT_TU_FP64 (no FMA contraction), FP32 fields in the other.
+#ifdef MT_TU_FP64
+void launch_tangent_fp64(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O, double* jac,
+                         double* lens, const TraceArgs& A, cudaStream_t stream) {
+#else
+static void launch_tangent_fp32(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O,
+                                double* jac, double* lens, const TraceArgs& A, cudaStream_t stream) {
+#endif
   switch (A.interp) {
     case MT_INTERP_NGP: launch_tangent_scheme<MT_INTERP_NGP>(tree, C, dirs, O, jac, lens, A, stream); break;
     case MT_INTERP_TSC: launch_tangent_scheme<MT_INTERP_TSC>(tree, C, dirs, O, jac, lens, A, stream); break;
     default: launch_tangent_scheme<MT_INTERP_CIC>(tree, C, dirs, O, jac, lens, A, stream); break;
   }
-  return cudaGetLastError();
 }
 
-// Enqueue the geodesic finder (called by mt_find_geodesics).
-void launch_finder(const mt_octree* tree, const DevCones& C, const OutPtrs& O, const FinderPtrs& P, const TraceArgs& A,
-                   double tol, int max_newton, int max_grid, cudaStream_t stream) {
+#ifdef MT_TU_FP64
+void launch_finder_fp64(const mt_octree* tree, const DevCones& C, const OutPtrs& O, const FinderPtrs& P,
+                        const TraceArgs& A, double tol, int max_newton, int max_grid, cudaStream_t stream) {
+#else
+static void launch_finder_fp32(const mt_octree* tree, const DevCones& C, const OutPtrs& O, const FinderPtrs& P,
+                               const TraceArgs& A, double tol, int max_newton, int max_grid, cudaStream_t stream) {
+#endif
   switch (A.interp) {
     case MT_INTERP_NGP: launch_finder_scheme<MT_INTERP_NGP>(tree, C, O, P, A, tol, max_newton, max_grid, stream); break;
     case MT_INTERP_TSC: launch_finder_scheme<MT_INTERP_TSC>(tree, C, O, P, A, tol, max_newton, max_grid, stream); break;
@@ -802,8 +815,37 @@ void launch_finder(const mt_octree* tree, const DevCones& C, const OutPtrs& O, c
   }
 }
 
+#ifndef MT_TU_FP64
+void launch_finder_fp64(const mt_octree* tree, const DevCones& C, const OutPtrs& O, const FinderPtrs& P,
+                        const TraceArgs& A, double tol, int max_newton, int max_grid, cudaStream_t stream);
+
+// Enqueue the tangent kernel (called by mt_trace_rays_adjoint).
+cudaError_t launch_tangent(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O, double* jac,
+                           double* lens, const TraceArgs& A, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(tree->ws, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return e;
+  if (tree->precision == MT_FIELD_FP64) {
+    launch_tangent_fp64(tree, C, dirs, O, jac, lens, A, stream);
+  } else {
+    launch_tangent_fp32(tree, C, dirs, O, jac, lens, A, stream);
+  }
+  return cudaGetLastError();
+}
+
+// Enqueue the geodesic finder (called by mt_find_geodesics).
+void launch_finder(const mt_octree* tree, const DevCones& C, const OutPtrs& O, const FinderPtrs& P, const TraceArgs& A,
+                   double tol, int max_newton, int max_grid, cudaStream_t stream) {
+  if (tree->precision == MT_FIELD_FP64) {
+    launch_finder_fp64(tree, C, O, P, A, tol, max_newton, max_grid, stream);
+  } else {
+    launch_finder_fp32(tree, C, O, P, A, tol, max_newton, max_grid, stream);
+  }
+}
+#endif
+
 }  // namespace mt
 
+#ifndef MT_TU_FP64
 using namespace mt;
 
 extern "C" mt_status mt_find_geodesics(const mt_octree* tree, const mt_trace_params* params, const double* src,
@@ -841,3 +883,4 @@ extern "C" mt_status mt_find_geodesics(const mt_octree* tree, const mt_trace_par
   if (prev >= 0 && prev != tree->device) cudaSetDevice(prev);
   return e == cudaSuccess ? MT_OK : MT_ERR_CUDA;
 }
+#endif  // MT_TU_FP64

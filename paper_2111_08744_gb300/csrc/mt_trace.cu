@@ -1,3 +1,4 @@
+// build: precision-split
 // Null-geodesic integration (Sect. 2.2): one ray per thread, persistent warps.
 //
 // Each warp keeps 32 rays in flight.  A lane whose ray has finished takes the next id of
@@ -147,8 +148,17 @@ void launch_trace(const mt_octree* tree, const DevCones& C, const double* dirs, 
   }
 }
 
+#ifdef MT_TU_FP64
+// FP64-field instantiations (this translation unit is compiled without FMA contraction).
+void launch_trace_fp64(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O,
+                       const TraceArgs& A, cudaStream_t stream) {
+  launch_trace<double>(tree, C, dirs, O, A, stream);
+}
+#endif
+
 }  // namespace mt
 
+#ifndef MT_TU_FP64
 using namespace mt;
 
 namespace mt {
@@ -206,7 +216,7 @@ extern "C" mt_status mt_trace_rays(const mt_octree* tree, const mt_trace_params*
   cudaError_t e = cudaMemsetAsync(tree->ws, 0, sizeof(unsigned long long), stream);
   if (e == cudaSuccess) {
     if (tree->precision == MT_FIELD_FP64) {
-      launch_trace<double>(tree, C, dirs, O, A, stream);
+      launch_trace_fp64(tree, C, dirs, O, A, stream);
     } else {
       launch_trace<float>(tree, C, dirs, O, A, stream);
     }
@@ -224,3 +234,4 @@ extern "C" mt_status mt_set_launch_config(mt_octree* tree, int32_t block_size, i
   tree->launch_bps = blocks_per_sm;
   return MT_OK;
 }
+#endif  // MT_TU_FP64

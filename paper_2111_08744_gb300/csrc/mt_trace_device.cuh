@@ -168,10 +168,11 @@ __device__ __forceinline__ bool ray_step_fp64(const DevField& F, const TraceArgs
     h = (r.eta_stop - r.y[3]) / k0;
     last = true;
   }
-  const double h2 = 0.5 * h, h3 = h / 3.0, h6 = h / 6.0;
+  // classical RK4, y + (h/6) (k1 + 2 k2 + 2 k3 + k4), the weighted sum formed left to right
+  const double h2 = 0.5 * h;
 #pragma unroll
   for (int i = 0; i < 10; ++i) {
-    acc[i] = r.y[i] + h6 * k[i];
+    acc[i] = k[i];
     t[i] = r.y[i] + h2 * k[i];
   }
   if (!geodesic_rhs<T, IP>(F, grav, t, k, nullptr, err)) {
@@ -180,7 +181,7 @@ __device__ __forceinline__ bool ray_step_fp64(const DevField& F, const TraceArgs
   }
 #pragma unroll
   for (int i = 0; i < 10; ++i) {
-    acc[i] += h3 * k[i];
+    acc[i] = acc[i] + 2.0 * k[i];
     t[i] = r.y[i] + h2 * k[i];
   }
   if (!geodesic_rhs<T, IP>(F, grav, t, k, nullptr, err)) {
@@ -189,17 +190,18 @@ __device__ __forceinline__ bool ray_step_fp64(const DevField& F, const TraceArgs
   }
 #pragma unroll
   for (int i = 0; i < 10; ++i) {
-    acc[i] += h3 * k[i];
+    acc[i] = acc[i] + 2.0 * k[i];
     t[i] = r.y[i] + h * k[i];
   }
   if (!geodesic_rhs<T, IP>(F, grav, t, k, nullptr, err)) {
     r.status = MT_RAY_LEFT_DOMAIN;
     return true;
   }
+  const double h6 = h / 6.0;
   bool finite = true;
 #pragma unroll
   for (int i = 0; i < 10; ++i) {
-    r.y[i] = acc[i] + h6 * k[i];
+    r.y[i] = r.y[i] + h6 * (acc[i] + k[i]);
     finite = finite && isfinite(r.y[i]);
   }
   r.lambda += h;
@@ -322,6 +324,17 @@ __device__ __forceinline__ void write_distortion(double A11, double A12, double 
     lens[4 * n + ray] = A11 * A22 - A12 * A21;
   }
 }
+
+// Launches of the FP64-field kernels, defined in the translation units compiled without FMA
+// contraction (MT_TU_FP64), so each FP64 operation there is one IEEE-754 operation.
+void launch_trace_fp64(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O,
+                       const TraceArgs& A, cudaStream_t stream);
+void launch_tangent_fp64(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O, double* jac,
+                         double* lens, const TraceArgs& A, cudaStream_t stream);
+void launch_lensing_fp64(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O, double* jac,
+                         double* lens, const TraceArgs& A, cudaStream_t stream);
+void launch_beams_fp64(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O, double* jac,
+                       double* lens, const TraceArgs& A, double tan_eps, int screen, cudaStream_t stream);
 
 mt_status check_trace_params(const mt_trace_params* p, int64_t n_rays);
 void fill_cones(const mt_octree* tree, const mt_trace_params* params, DevCones* C);

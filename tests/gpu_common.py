@@ -3,7 +3,12 @@ import numpy as np
 
 FLOAT_KEYS = ["x", "k", "eta", "lambda", "chi", "path", "z0", "z1", "z4", "z5", "d_a", "d_l", "phi_o", "phi_s", "isw"]
 INT_KEYS = ["n_steps", "level", "status"]
-TIE_MARGIN = 1e-8
+# A ray whose path grazes a cell face (or the stop surface) within a few ulps of its coordinates has
+# two valid index sequences; the oracle reports each ray's smallest decision margin ("tie").  With
+# the FP64 path evaluating the method's expressions as IEEE operations in the definition's order,
+# index mismatches are allowed only on rays whose margin is below this ulp-scale bound, and the
+# number of such exempted rays is counted and bounded by each test (0 unless stated).
+TIE_MARGIN = 1e-12
 # absolute floors of the relative error: lengths in h^-1 Mpc, redshifts, potentials, wave vector
 FLOORS = {"x": 1.0, "k": 1.0, "eta": 1.0, "lambda": 1.0, "chi": 1.0, "path": 1.0, "d_a": 1.0, "d_l": 1.0,
           "z0": 1e-6, "z1": 1e-6, "z4": 1e-6, "z5": 1e-6, "phi_o": 1e-6, "phi_s": 1e-6, "isw": 1e-6}
@@ -34,30 +39,40 @@ def rel_err(got, ref, key):
     return np.abs(got - ref) / np.maximum(np.abs(ref), FLOORS[key])
 
 
-def compare(got, ref, rtol, exact_ints=True, idx=None, keys=None):
-    """Element-wise comparison; returns the max relative error per float output."""
+def compare(got, ref, rtol, exact_ints=True, idx=None, keys=None, max_exempt=0):
+    """Element-wise comparison; returns the max relative error per float output and, under
+    "exempt", the number of rays whose index mismatch was accepted as a tie (at most max_exempt)."""
     errs = {}
+    exempt = set()
     for k in INT_KEYS:
         g, r = got[k], ref[k]
         if idx is not None:
             g = g[..., idx]
         if exact_ints:
             bad = np.nonzero(g != r)[0]
-            # a ray whose path grazes a cell face within rounding has two valid index sequences
-            # (two correct answers); every mismatch must be such a tie, and ties must be rare
             tie = ref.get("tie")
             if tie is not None and bad.size:
                 untied = bad[tie[bad] >= TIE_MARGIN]
                 assert untied.size == 0, (f"{k} differs on {untied.size} non-tie rays, first {untied[:5]}: "
                                           f"gpu {g[untied[:5]]} oracle {r[untied[:5]]} tie {tie[untied[:5]]}")
-                assert bad.size <= max(2, 0.01 * g.size), f"{k}: too many tie mismatches ({bad.size})"
+                exempt.update(int(i) for i in bad)
             else:
                 assert bad.size == 0, f"{k} differs on {bad.size} rays, first {bad[:5]}: gpu {g[bad[:5]]} oracle {r[bad[:5]]}"
+    if exact_ints:
+        print(f"index mismatches exempted as ties below {TIE_MARGIN:g}: {len(exempt)} of {got['n_steps'][..., idx].size if idx is not None else got['n_steps'].size} rays")
+        assert len(exempt) <= max_exempt, f"{len(exempt)} tie exemptions (at most {max_exempt}): {sorted(exempt)[:10]}"
+    keep = None
+    if exempt:
+        keep = np.ones(got["n_steps"][..., idx].size if idx is not None else got["n_steps"].size, bool)
+        keep[sorted(exempt)] = False
     for k in (keys or FLOAT_KEYS):
         g, r = got[k], ref[k]
         if idx is not None:
             g = g[..., idx]
+        if keep is not None:
+            g, r = g[..., keep], r[..., keep]
         e = rel_err(g, r, k)
         errs[k] = float(e.max()) if e.size else 0.0
         assert errs[k] <= rtol, f"{k}: max relative error {errs[k]:.3e} > {rtol:.1e}"
+    errs["exempt"] = len(exempt)
     return errs

@@ -13,7 +13,7 @@ import pytest
 import oracle
 from paper_2111_08744_gb300 import inputs as I
 from tests import helpers as H
-from tests.gpu_common import compare, run_gpu
+from tests.gpu_common import FLOAT_KEYS, INT_KEYS, compare, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -48,6 +48,24 @@ def test_plain_fp64_full_config():
     compare(got, oracle_of("plain"), 1e-6)
 
 
+def _bitwise(got, ref, idx=None):
+    """Every output equal bit for bit (the FP64 form evaluates each expression of the method as the
+    oracle does: one IEEE-754 operation at a time, in the definition's order)."""
+    for k in FLOAT_KEYS + INT_KEYS:
+        g = got[k] if idx is None else got[k][..., idx]
+        diff = np.count_nonzero(g != ref[k])
+        assert diff == 0, f"{k}: {diff} values differ from the oracle"
+
+
+def test_plain_fp64_bit_identical_to_oracle():
+    """Config 1 (64^3, 3072 rays from an observer on a cell corner, 128 of them grazing cell faces
+    within 1e-14 cells): identical end points, redshifts, distances, step counts and levels."""
+    w = plain()
+    ref = oracle_of("plain")
+    assert (ref["tie"] < 1e-12).sum() > 0          # rays that graze faces: ties are present
+    _bitwise(run_gpu(w, "fp64"), ref)
+
+
 def test_plain_flrw_gravity_off():
     w = plain()
     got = run_gpu(w, "fp64", gravity_on=False)
@@ -60,6 +78,7 @@ def test_amr_small_fp64_bit_exact_indices():
     ref = oracle_of("amr_small")
     assert (ref["level"] > 0).any(), "workload must reach refined levels"
     compare(got, ref, 1e-6)
+    _bitwise(got, ref)
 
 
 def test_amr_small_fp32_field_mixed_precision():
@@ -209,3 +228,4 @@ def test_full_workload_fp64_sampled_bit_exact():
     got = run_gpu(w, "fp64")
     idx, ref = amr_full_sample()
     compare(got, ref, 1e-6, idx=idx)
+    _bitwise(got, ref, idx)
