@@ -36,30 +36,92 @@ FIELD_BYTES_PER_STEP = 4 * 8 * 16 * 2   # 4 stages x 8 CIC records x 16 B (float
 FIELD_BYTES_BY_SCHEME = {"ngp": 4 * 1 * 16 * 2, "cic": FIELD_BYTES_PER_STEP, "tsc": 4 * 27 * 16 * 2}
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one full launch of
-# trace_kernel<float> on the benchmark workload, from one single-pass ncu capture, with the
-# SHA-256 of the kernel's sources at capture time: reported only while they are unchanged.
+# ncu record of trace_kernel<float> on the benchmark workload, with the SHA-256 of the kernel's code
+# (its sources with comments removed) at capture time; reported only while that code is unchanged.
+#   dram_bytes_per_launch: dram__bytes_read.sum + dram__bytes_write.sum of one full launch (a
+#       single-pass capture of the benchmark command);
+#   per_rk4_step: smsp__inst_executed.sum (warp instructions) and smsp__inst_executed_pipe_fp64.sum
+#       (warp instructions on the FP64 pipe) divided by the RK4 steps of the captured launch (the
+#       65,536-ray profiling launch, --set full);
+#   pct: the same capture's sm__pipe_fp64_cycles_active, smsp__issue_active, sm__warps_active
+#       (percent of peak) and active lanes per instruction.
 TRACE_KERNEL_SOURCES = ["include/mt.h", "paper_2111_08744_gb300/csrc/mt_internal.cuh",
                         "paper_2111_08744_gb300/csrc/mt_mixed.cuh", "paper_2111_08744_gb300/csrc/mt_trace_device.cuh",
                         "paper_2111_08744_gb300/csrc/mt_trace.cu"]
-NCU_TRAFFIC = {"bytes_per_launch": 57.97e9 + 0.964e9,
-               "sources_sha256": "384ab8f7380c8f8146e507bfd018fd98cf9288790942ac5723797e3c5785c96e"}
+NCU_RECORD = {"sources_sha256": "",
+              "dram_bytes_per_launch": None,
+              "per_rk4_step": {"warp_inst": None, "fp64_warp_inst": None},
+              "pct": {}}
+SMS, SCHEDULERS_PER_SM = 152, 4
+
+
+def _strip_comments(text: str) -> str:
+    """C/C++ source without // and /* */ comments (string and character literals kept), with every
+    run of white space reduced to one blank."""
+    import re
+    pat = re.compile(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\])*"|\'(?:\\.|[^\'\\])*\'', re.S)
+    code = pat.sub(lambda m: m.group(0) if m.group(0)[0] in "\"'" else " ", text)
+    return " ".join(code.split())
 
 
 def trace_kernel_sha256():
+    """SHA-256 of the trace kernel's code: its sources with the comments removed, so that a change
+    of comments keeps the ncu record and a change of code drops it."""
     import hashlib
     h = hashlib.sha256()
     for rel in TRACE_KERNEL_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(rel.encode() + b"\0" + f.read())
+        with open(os.path.join(ROOT, rel)) as f:
+            h.update(rel.encode() + b"\0" + _strip_comments(f.read()).encode())
     return h.hexdigest()
+
+
+def ncu_record():
+    """The ncu record of the trace kernel, or None once the kernel's code changed since the capture."""
+    if NCU_RECORD["sources_sha256"] and NCU_RECORD["sources_sha256"] == trace_kernel_sha256():
+        return NCU_RECORD
+    return None
 
 
 def measured_traffic():
     """ncu DRAM bytes of one trace launch, or None once the kernel changed since the capture."""
-    if NCU_TRAFFIC["sources_sha256"] and NCU_TRAFFIC["sources_sha256"] == trace_kernel_sha256():
-        return NCU_TRAFFIC["bytes_per_launch"]
-    return None
+    rec = ncu_record()
+    return rec["dram_bytes_per_launch"] if rec else None
+
+
+def roofline(total_steps, ms, sm_mhz, fp64_fma_per_s, hbm_gbs, field_bytes, record, peaks_source):
+    """Roofline of the trace kernel.  The binding resource is arithmetic issue, not HBM (the field
+    gathers are served by shared memory, L1 and L2): the headline is the FP64 pipe -- FP64 warp
+    instructions per RK4 step (ncu) x 32 lanes x RK4 steps per second (CUDA events), against the FP64
+    FMA lane rate measured on this GPU by mt_probe_fp64_fma_rate -- with the issue-slot fraction, the
+    DRAM fraction (ncu traffic) and the algorithmic field bandwidth ("effective") beside it."""
+    t = ms * 1e-3
+    steps_per_s = total_steps / t
+    eff = field_bytes * steps_per_s / 1e9
+    out = {"bound": "alu", "unit": "G FP64 lane-ops/s", "achieved": None, "peak": fp64_fma_per_s / 1e9,
+           "frac": None, "traffic": None, "kernel": "trace_kernel<float>",
+           "peak_source": "mt_probe_fp64_fma_rate, measured in this run (of measured)",
+           "limiter": "latency-bound issue: FP64 pipe and issue slots share the time, DRAM is not the limit",
+           "hbm_effective": {"algorithmic_bytes_per_rk4_step": field_bytes, "achieved_GBs": eff, "peak_GBs": hbm_gbs,
+                             "frac": eff / hbm_gbs, "peak_source": peaks_source},
+           "rk4_steps_per_launch": total_steps}
+    if record is None:
+        out["ncu_record"] = "stale: the trace kernel changed since the last ncu capture"
+        return out
+    per = record["per_rk4_step"]
+    if per.get("fp64_warp_inst"):
+        ach = per["fp64_warp_inst"] * 32 * steps_per_s
+        out["achieved"] = ach / 1e9
+        out["frac"] = ach / fp64_fma_per_s
+    if per.get("warp_inst") and sm_mhz:
+        issue_peak = SMS * SCHEDULERS_PER_SM * sm_mhz * 1e6
+        out["issue"] = {"achieved_ginst_s": per["warp_inst"] * steps_per_s / 1e9, "peak_ginst_s": issue_peak / 1e9,
+                        "frac": per["warp_inst"] * steps_per_s / issue_peak}
+    if record.get("dram_bytes_per_launch"):
+        out["traffic"] = record["dram_bytes_per_launch"]
+        dram = record["dram_bytes_per_launch"] / t / 1e9
+        out["dram"] = {"achieved_GBs": dram, "peak_GBs": hbm_gbs, "frac": dram / hbm_gbs}
+    out["ncu_pct"] = record.get("pct", {})
+    return out
 
 
 def workload_config(w):
@@ -286,13 +348,10 @@ def run_ours(args, ws, rank):
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    field_bytes = FIELD_BYTES_BY_SCHEME[args.interp]
-    achieved = field_bytes * total_steps / (ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-            "traffic": measured_traffic() if (args.rays == 0 and args.interp == "cic") else None,
-            "kernel": "trace_kernel<float>",
-            "algorithmic_bytes_per_rk4_step": field_bytes, "rk4_steps_per_launch": total_steps,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+    fp64_rate = B.probe_fp64_fma_rate()
+    record = ncu_record() if (args.rays == 0 and args.interp == "cic") else None
+    roof = roofline(total_steps, ms, ck.get("sm_mhz"), fp64_rate, hbm_peak, FIELD_BYTES_BY_SCHEME[args.interp],
+                    record, "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s")
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, ns, threads, dt = oracle_sample(w, budget_s=args.ref_budget, interp=args.interp)
@@ -474,15 +533,16 @@ def run_large(args, ws, rank):
     except Exception:
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = FIELD_BYTES_PER_STEP * steps / (ms * 1e-3) / 1e9
+    # the ncu record's per-step counts belong to the benchmark workload, not to this one
+    roof = roofline(steps, ms, ck.get("sm_mhz"), B.probe_fp64_fma_rate(), hbm, FIELD_BYTES_PER_STEP, None,
+                    "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s")
     line = {"metric": "rays/s to z=2, largest AMR configuration", "value": n / (ms * 1e-3), "unit": "rays/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 state / f32 field", "data": "synthetic",
             "config": {"workload": w.name, "n_rays": n, "cells_per_level": cells, "device_bytes_octree": nbytes,
                        "n_slices": w.n_slices, "z_max": float(w.z_max[0])},
             "steps_per_s": steps / (ms * 1e-3), "rk4_steps_per_step": steps,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": None, "kernel": "trace_kernel<float>"},
+            "roofline": roof,
             "generation_s": t_gen, "build_s": t_build, "device_status": st, "ray_status_counts": status,
             "end_level_counts": levels[1:], "clocks": ck, "step_ms_all": ts, "gpu_launches": args.steps}
     if tangent is not None:
@@ -494,8 +554,10 @@ def run_large(args, ws, rank):
 
 def run_diff(args, ws, rank):
     """Differentiation: 1024 x 1024 rays over 10 x 10 deg to z = 1 through the 128^3 + 3 levels
-    field (FP64 records); timings of the forward trace, the forward-mode distortion matrix and the
-    reverse-mode gradient of L = sum |xi - xi_FLRW|^2 with respect to the records and to phi_0."""
+    field; timings of the forward trace, the forward-mode distortion matrix and the reverse-mode
+    gradient of L = sum |xi - xi_FLRW|^2 with respect to the records and to phi_0, on the FP32 copy of
+    the records (mixed step: FP32 stages, FP64 state) and on the FP64 records (the FP64 reverse sweep
+    on a seeded 1/16 of the rays unless --diff-fp64-reverse)."""
     import torch
 
     from paper_2111_08744_gb300 import binding as B
@@ -505,7 +567,6 @@ def run_diff(args, ws, rank):
     Bd.build()
     w = I.cached(I.config_diff, n_pix=args.diff_pix)
     dev = torch.device("cuda", torch.cuda.current_device())
-    tree = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, w.levels, w.bg, "fp64")
     params = B.TraceParams.from_workload(w)
     dirs = torch.from_numpy(w.dirs).to(dev)
     n = w.n_rays
@@ -518,45 +579,81 @@ def run_diff(args, ws, rank):
         torch.cuda.synchronize()
         return r, a.elapsed_time(b)
 
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    # reference end points: the same rays traced without gravity (FLRW)
+    tree = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, w.levels, w.bg, "fp64")
+    ref = B.trace_rays(tree, B.TraceParams.from_workload(w, gravity_on=False), dirs)["xi"]
+    # FP64 records: forward, distortion matrix, reverse sweep (on a sample of the rays by default)
     out, _ = timed(lambda: B.trace_rays(tree, params, dirs))
     out, ms_fwd = timed(lambda: B.trace_rays(tree, params, dirs))
     steps = int(out["n_steps"].sum().item())
     tan, ms_tan = timed(lambda: B.trace_rays_adjoint(tree, params, dirs, jacobian=True, lensing=True))
-    # reference end points: the same rays traced without gravity (FLRW)
-    ref = B.trace_rays(tree, B.TraceParams.from_workload(w, gravity_on=False), dirs)["xi"]
     dxi = 2.0 * (tan["xi"] - ref)
-    adj, ms_adj = timed(lambda: B.trace_rays_adjoint(tree, params, dirs, jacobian=False, lensing=False,
-                                                     dL_dxi=dxi, checkpoint_every=64))
-    g0, ms_pb = timed(lambda: B.pullback_coarse_phi(tree, adj["dL_drec"], w.slice_weight, w.n_coarse))
     lens = tan["lens"]
-    # the same rays on the FP32 copy of the records: mixed trace and mixed tangent step
+    if args.diff_fp64_reverse:
+        sub = torch.arange(n, device=dev)
+    else:
+        rng = np.random.Generator(np.random.PCG64(4114))
+        sub = torch.from_numpy(np.sort(rng.choice(n, size=n // 16, replace=False))).to(dev)
+    p_sub = B.TraceParams(w.observer, w.z_max, [0, int(sub.numel())], w.steps_per_cell,
+                          max_steps=params.c.max_steps)
+    d_sub = dirs[:, sub].contiguous()
+    adj, ms_adj64 = timed(lambda: B.trace_rays_adjoint(tree, p_sub, d_sub, jacobian=False, lensing=False,
+                                                       dL_dxi=dxi[:, sub].contiguous(), checkpoint_every=64))
+    steps_sub = int(adj["n_steps"].sum().item())
+    g0_64, ms_pb = timed(lambda: B.pullback_coarse_phi(tree, adj["dL_drec"], w.slice_weight, w.n_coarse))
     del adj
+    tree.free()
+    # FP32 copy of the records: mixed trace, mixed tangent, mixed reverse sweep on every ray
     tree32 = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, I.fp32_levels(w), w.bg, "fp32")
     B.trace_rays(tree32, params, dirs)
     out32, ms_fwd32 = timed(lambda: B.trace_rays(tree32, params, dirs))
+    steps32 = int(out32["n_steps"].sum().item())
     tan32, ms_tan32 = timed(lambda: B.trace_rays_adjoint(tree32, params, dirs, jacobian=True, lensing=True))
     dA = (tan32["jac"] - tan["jac"]).abs()
     dk = (tan32["lens"][0] - lens[0]).abs()
-    steps32 = int(out32["n_steps"].sum().item())
-    mixed = {"forward_ms": ms_fwd32, "tangent_ms": ms_tan32, "forward_steps_per_s": steps32 / (ms_fwd32 * 1e-3),
-             "tangent_steps_per_s": steps32 / (ms_tan32 * 1e-3), "jac_abs_diff_vs_fp64_max": float(dA.max()),
-             "jac_abs_diff_vs_fp64_median": float(dA.median()), "kappa_abs_diff_median": float(dk.median()),
-             "kappa_abs_diff_p99": float(torch.quantile(dk[:1 << 20], 0.99))}
+    dxi32 = 2.0 * (tan32["xi"] - ref)
+    rev = {}
+    for ce in args.diff_checkpoints:
+        adj32, ms = timed(lambda: B.trace_rays_adjoint(tree32, params, dirs, jacobian=False, lensing=False,
+                                                       dL_dxi=dxi32, checkpoint_every=ce))
+        rev[ce] = ms
+    g0_32, _ = timed(lambda: B.pullback_coarse_phi(tree32, adj32["dL_drec"], w.slice_weight, w.n_coarse))
+    # the mixed reverse sweep on the sampled rays, against the FP64 one on the same rays
+    adj32s = B.trace_rays_adjoint(tree32, p_sub, d_sub, jacobian=False, lensing=False,
+                                  dL_dxi=dxi[:, sub].contiguous(), checkpoint_every=64)
+    g0_32s = B.pullback_coarse_phi(tree32, adj32s["dL_drec"], w.slice_weight, w.n_coarse)
+    torch.cuda.synchronize()
+    rel_grad = float((g0_32s - g0_64).norm() / g0_64.norm())
+    ck = clocks.stop()
+    best_ce = min(rev, key=rev.get)
+    mixed = {"forward_ms": ms_fwd32, "tangent_ms": ms_tan32, "reverse_ms_by_checkpoint_interval": rev,
+             "forward_steps_per_s": steps32 / (ms_fwd32 * 1e-3),
+             "tangent_steps_per_s": steps32 / (ms_tan32 * 1e-3),
+             "reverse_steps_per_s": steps32 / (rev[best_ce] * 1e-3),
+             "reverse_over_forward": rev[best_ce] / ms_fwd32,
+             "jac_abs_diff_vs_fp64_max": float(dA.max()), "jac_abs_diff_vs_fp64_median": float(dA.median()),
+             "kappa_abs_diff_median": float(dk.median()),
+             "kappa_abs_diff_p99": float(torch.quantile(dk[:1 << 20], 0.99)),
+             "grad_phi0_rel_l2_diff_vs_fp64_sample": rel_grad,
+             "grad_phi0_rms": float(g0_32.std().item())}
     tree32.free()
     line = {"metric": "differentiable ray tracing: forward, distortion matrix and gradient time",
-            "value": n / (ms_tan * 1e-3), "unit": "rays/s (distortion matrix)", "n_gpus": ws,
-            "steps": 1, "warmup": 1, "ms_per_step": ms_tan, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "n_rays": n, "rk4_steps": steps, "checkpoint_every": 64},
-            "forward_ms": ms_fwd, "tangent_ms": ms_tan, "adjoint_ms": ms_adj, "pullback_ms": ms_pb,
-            "forward_steps_per_s": steps / (ms_fwd * 1e-3), "tangent_steps_per_s": steps / (ms_tan * 1e-3),
-            "adjoint_steps_per_s": steps / (ms_adj * 1e-3),
+            "value": n / (rev[best_ce] * 1e-3), "unit": "rays/s (reverse sweep, mixed)", "n_gpus": ws,
+            "steps": 1, "warmup": 1, "ms_per_step": rev[best_ce], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 state / f32 field", "data": "synthetic",
+            "config": {"workload": w.name, "n_rays": n, "rk4_steps": steps, "checkpoint_every": best_ce},
+            "mixed_fp32_field": mixed,
+            "fp64_field": {"forward_ms": ms_fwd, "tangent_ms": ms_tan, "forward_steps_per_s": steps / (ms_fwd * 1e-3),
+                           "tangent_steps_per_s": steps / (ms_tan * 1e-3), "reverse_rays": int(sub.numel()),
+                           "reverse_ms": ms_adj64, "reverse_steps_per_s": steps_sub / (ms_adj64 * 1e-3),
+                           "pullback_ms": ms_pb},
             "kappa_rms": float(lens[0].std().item()), "gamma_rms": float(lens[1:3].std().item()),
             "omega_rms": float(lens[3].std().item()), "loss": float(((tan["xi"] - ref) ** 2).sum().item()),
-            "grad_phi0_rms": float(g0.std().item()), "mixed_fp32_field": mixed, "gpu_launches": 8}
+            "clocks": ck, "gpu_launches": 8 + 2 * len(rev)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    tree.free()
 
 
 def main():
@@ -576,6 +673,10 @@ def main():
     ap.add_argument("--large-tangent", action="store_true",
                     help="large workload: also time the distortion-matrix pass on every ray")
     ap.add_argument("--diff-pix", type=int, default=1024)
+    ap.add_argument("--diff-fp64-reverse", action="store_true",
+                    help="diff workload: FP64 reverse sweep on every ray (default: a seeded 1/16)")
+    ap.add_argument("--diff-checkpoints", type=int, nargs="+", default=[64, 16],
+                    help="diff workload: checkpoint intervals of the mixed reverse sweep to time")
     ap.add_argument("--interp", default="cic", choices=["cic", "ngp", "tsc"],
                     help="amr workload: interpolation scheme (Sect. 2.2; the benchmark line is CIC)")
     args = ap.parse_args()

@@ -134,7 +134,7 @@ typedef enum { MT_INTERP_CIC = 0, MT_INTERP_NGP = 1, MT_INTERP_TSC = 2 } mt_inte
 /*
  * Trace parameters.  Rays [ray_begin[c], ray_begin[c+1]) belong to cone c
  * with observer observer[c] at eta_o and stop on the iso-eta surface
- * eta_stop(c) = eta(a = 1 / (1 + z_max[c])) (Sect. 2.4 stop criterion, here
+ * eta_stop(c) = eta(a = 1 / (1 + z_max[c])) (Sects. 2.3.2 and 2.4: the stop criterion, here
  * p = eta), found by bisection on the background interpolant.
  */
 typedef struct {
@@ -221,11 +221,13 @@ mt_status mt_trace_rays(const mt_octree* tree, const mt_trace_params* params, co
  * counts each ray's steps, allocates a temporary checkpoint buffer (8 doubles per
  * checkpoint), runs the sweep and frees it.  Rays that do not end with MT_RAY_OK add nothing.
  *
- * Forward mode integrates each ray as mt_trace_rays does: FP64 arithmetic on an FP64 octree;
- * on an FP32 octree the mixed step (FP32 stages, FP64 state) with FP32 stage derivatives and an
- * FP64 tangent state.  Reverse mode integrates in FP64 arithmetic (records of the octree's
- * precision) and supports MT_INTERP_CIC only (others: MT_ERR_UNSUPPORTED).  Both write the ray
- * outputs `out` (NULL pointers skip an output) of their integration.
+ * Both modes integrate each ray as mt_trace_rays does and differentiate that map: FP64
+ * arithmetic on an FP64 octree; on an FP32 octree the mixed step (FP32 stages, FP64 state) with
+ * FP32 stage derivatives and an FP64 tangent / cotangent state (reverse mode: per-lane FP32
+ * accumulation of the record cotangents, added to dL_drec with FP64 atomics).  Reverse mode
+ * supports MT_INTERP_CIC only (others: MT_ERR_UNSUPPORTED).  Both write the ray outputs `out`
+ * (NULL pointers skip an output) of their integration.  A smaller checkpoint_every recomputes
+ * less (1: every state is kept) at 8 doubles per checkpoint.
  * Errors: as mt_trace_rays; MT_ERR_INVALID_ARG if neither mode is requested or reverse-mode
  * arguments are incomplete; MT_ERR_OOM if the checkpoint buffer cannot be allocated.
  */
@@ -233,6 +235,23 @@ mt_status mt_trace_rays_adjoint(const mt_octree* tree, const mt_trace_params* pa
                                 int64_t n_rays, const mt_ray_out* out, double* jac, double* lens,
                                 const double* dL_dxi, double* const* dL_drec, int32_t checkpoint_every,
                                 void* stream);
+
+/*
+ * mt_trace_rays_jvp -- forward-mode derivative of the end points with respect to the gridded
+ * potential records: dxi = J v for the map records -> xi (xi = x - (k / k0)(eta - eta_stop), the
+ * end point on the iso-eta surface), the Jacobian-vector product whose transpose the reverse mode
+ * of mt_trace_rays_adjoint applies.  The same differentiable discrete map: RK4 stages of Eqs.
+ * (2)-(4), CIC weights (Eq. 8) at the level and slices the trace uses, the step size and the
+ * shortened last step, and phi at the observer in the initial wave vector.
+ * d_rec: [n_levels + 1] device FP64 buffers [count_l][n_slices][4] (same layout as the records; a
+ * NULL entry is a zero perturbation on that level).  dxi: device [3][N], overwritten (0 for rays
+ * that do not end with MT_RAY_OK).  `out` receives the rays' outputs (NULL pointers skip them).
+ * FP64 arithmetic, records of the octree's precision; MT_INTERP_CIC only (others:
+ * MT_ERR_UNSUPPORTED).  Asynchronous on `stream`; allocates nothing.
+ * Errors: as mt_trace_rays; MT_ERR_INVALID_ARG for NULL d_rec or dxi.
+ */
+mt_status mt_trace_rays_jvp(const mt_octree* tree, const mt_trace_params* params, const double* dirs, int64_t n_rays,
+                            const mt_ray_out* out, const double* const* d_rec, double* dxi, void* stream);
 
 /*
  * mt_trace_rays_lensing -- the infinitesimal-beam distortion matrix of Sect. 2.3.1 along each
@@ -274,7 +293,7 @@ mt_status mt_trace_beams(const mt_octree* tree, const mt_trace_params* params, c
                          double eps, int32_t screen, const mt_ray_out* out, double* jac, double* lens, void* stream);
 
 /*
- * mt_find_geodesics -- geodesic finder (Sect. 2.6): for each source at comoving position
+ * mt_find_geodesics -- geodesic finder (Sect. 2.5): for each source at comoving position
  * src[:, i] (device [3][N], absolute box coordinates; source i belongs to the cone of params,
  * whose observer x_o it uses; z_max is ignored), the observed direction theta at x_o whose ray,
  * stopped on the sphere |x - x_o| = chi_s = |src - x_o| (the end point moved back along k onto it),
@@ -296,7 +315,7 @@ mt_status mt_find_geodesics(const mt_octree* tree, const mt_trace_params* params
                             double* jac, double* resid, int32_t* iters, int32_t* status, void* stream);
 
 /*
- * mt_healpix_bin -- HEALPix maps of per-ray quantities (Sect. 2.5 map products: lensing,
+ * mt_healpix_bin -- HEALPix maps of per-ray quantities (Sect. 2.4 map products: lensing,
  * lensing_born, deflection, phi, isw, steps, relative differences...).  Each direction
  * dirs[:, i] (device [3][n], any length) gets its pixel at resolution nside (a power of two,
  * <= 2^28) in the NESTED (nest = 1) or RING (nest = 0) numbering of Gorski et al. (2005), and
@@ -310,7 +329,7 @@ mt_status mt_healpix_bin(const double* dirs, int64_t n, const double* values, in
                          double* sums, double* counts, int64_t* ipix, void* stream);
 
 /*
- * mt_deflection -- the deflection angle of Sect. 2.5, alpha = theta - beta, for rays traced with
+ * mt_deflection -- the deflection angle of Sect. 2.4, alpha = theta - beta, for rays traced with
  * params (the cone table gives each ray's observer): theta = dirs[:, i] (observed direction),
  * beta = the direction of xi[:, i] - x_o (xi: end points on the stop surface, device [3][N], as
  * written by the trace calls).  alpha: device [3][N] = the components of theta^ - beta^ on the
@@ -383,6 +402,17 @@ mt_status mt_set_launch_config(mt_octree* tree, int32_t block_size, int32_t bloc
  * clear it.
  */
 mt_status mt_device_status(const mt_octree* tree, void* stream);
+
+/*
+ * mt_probe_fp64_fma_rate -- measured FP64 fused multiply-add rate of the current device, in
+ * lane-operations per second (one FMA of one thread = 1): the denominator of the FP64-pipe
+ * roofline reported for the trace kernels.  Not part of the method (the paper has no
+ * counterpart): a calibration kernel of independent FMA chains, `iters` per chain, launched
+ * num_SMs x (resident blocks) times `repeats` + 1 on `stream` (the first launch warms up), timed
+ * with CUDA events; *fma_per_s receives the best rate.  Synchronous; allocates nothing.
+ * Errors: MT_ERR_INVALID_ARG (NULL output, iters < 1, repeats < 1), MT_ERR_CUDA.
+ */
+mt_status mt_probe_fp64_fma_rate(int64_t iters, int32_t repeats, double* fma_per_s, void* stream);
 
 /* mt_free -- release everything mt_build_octree allocated (NULL is ignored).
  * The caller must make sure no enqueued work still uses the octree. */

@@ -145,7 +145,7 @@ def trace(w, dirs=None, levels=None, gravity_on=True, max_steps=10_000_000, n_th
 
     interp: "cic" (Eq. 8), "ngp" (Eq. 7) or "tsc" (Eq. 9), each with the level fallback of Sect. 2.2.
     chi_stop: per-ray comoving distances [N]: stop on the sphere |x - x_o| = chi_stop (the geodesic
-    finder's criterion, Sect. 2.6) instead of the iso-eta surface of z_max.
+    finder's criterion, Sect. 2.5) instead of the iso-eta surface of z_max.
 
     Besides the per-ray outputs of the method, "tie" is the smallest margin of any index
     decision along the ray: the distance (in cell units) of a floor() argument to the

@@ -418,7 +418,7 @@ struct Tracer {
     }
   };
 
-  // chi_stop > 0: the iso-chi stop of the geodesic finder (Sect. 2.6): the ray steps as usual
+  // chi_stop > 0: the iso-chi stop of the geodesic finder (Sect. 2.5): the ray steps as usual
   // until its comoving distance |x - x_o| reaches chi_stop, and the end point is then moved back
   // along k onto that sphere: x - t k with the smaller root t of |x - t k - x_o| = chi_stop (and
   // eta - t k0).  eta_stop then only bounds the integration.
@@ -648,57 +648,86 @@ static int trace_rays_impl(const orc_grid* g, const orc_level* lv, const double*
   return 0;
 }
 
-// HEALPix pixel of direction v (Gorski et al. 2005, the sky pixelisation of Sect. 2.5): z = cos(theta),
-// t = phi / (pi/2) in [0, 4).  Equatorial zone |z| <= 2/3: the pixel is fixed by the two edge-line
-// indices jp = floor(N (1/2 + t) - 3N z / 4) and jm = floor(N (1/2 + t) + 3N z / 4); polar caps: by
-// jp = floor(tp s), jm = floor((1 - tp) s) with s = N sqrt(3 (1 - |z|)), tp the position in the
-// quarter.  RING numbers rings from the north pole; NESTED numbers the 12 base faces and
-// interleaves the in-face (x, y) bits.
+// HEALPix pixel of direction v (Gorski et al. 2005, the sky pixelisation of Sect. 2.4), written
+// through the HEALPix projection of the sphere onto the plane (Calabretta & Roukema 2007), in which
+// every pixel boundary is a straight line at 45 degrees.  In units of pi/4:
+//   equatorial zone |z| <= 2/3:  X = phi / (pi/4),  Y = 3 z / 2;
+//   polar caps |z| > 2/3:        s = sqrt(3 (1 - |z|)),  X = X_c + (phi / (pi/4) - X_c) s,
+//                                Y = sign(z) (2 - s),  X_c = 2 q + 1 the centre of the quarter q of phi.
+// In the rotated coordinates p = X + Y, m = X - Y the 12 base pixels are the squares
+// [2P - 1, 2P + 1) x [2M - 1, 2M + 1): P = M is an equatorial face (4 + P mod 4), P = M + 1 a
+// northern one (M mod 4), M = P + 1 a southern one (8 + P mod 4).  Inside a face, the pixel
+// coordinates run along p (ix, from the south corner towards the east one) and along -m (iy,
+// towards the west one) in N steps.  Rings are horizontal lines of Y (ring i through the pixel
+// centres at Y = 2 - i / N), so the ring of (ix, iy) is j_f N - ix - iy - 1 with j_f = 3 - Y_c
+// (Y_c the face centre), and its place along the ring follows from X.
 static int64_t healpix_pixel(int64_t N, const double* v, bool nest) {
-  double r = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-  double z = v[2] / r, za = std::fabs(z);
-  double ph = std::atan2(v[1], v[0]);
   const double pi = 3.14159265358979323846;
+  const double r = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  const double z = v[2] / r;
+  double ph = std::atan2(v[1], v[0]);
   if (ph < 0.0) ph += 2.0 * pi;
-  double t = ph / (0.5 * pi);
-  if (t >= 4.0) t -= 4.0;
-  int64_t npix = 12 * N * N, ncap = 2 * N * (N - 1);
-  if (za <= 2.0 / 3.0) {
-    double a = N * (0.5 + t), b = 0.75 * N * z;
-    int64_t jp = (int64_t)std::floor(a - b), jm = (int64_t)std::floor(a + b);
-    if (!nest) {
-      int64_t ir = N + 1 + jp - jm;                 // ring counted from z = 2/3, 1 .. 2N + 1
-      int64_t shift = 1 - (ir & 1);
-      int64_t ip = (jp + jm - N + shift + 1) / 2;
-      ip = ((ip % (4 * N)) + 4 * N) % (4 * N);
-      return ncap + (ir - 1) * 4 * N + ip;
-    }
-    int64_t fp = jp / N, fm = jm / N;
-    int64_t face = fp == fm ? (fp | 4) : (fp < fm ? fp : fm + 8);
-    int64_t ix = jm & (N - 1), iy = N - (jp & (N - 1)) - 1;
+  double X = ph / (0.25 * pi);
+  if (X >= 8.0) X -= 8.0;
+  double Y;
+  if (std::fabs(z) <= 2.0 / 3.0) {
+    Y = 1.5 * z;
+  } else {
+    const double s = std::sqrt(3.0 * (1.0 - std::fabs(z)));
+    double q = std::floor(0.5 * X);
+    if (q > 3.0) q = 3.0;
+    const double xc = 2.0 * q + 1.0;
+    X = xc + (X - xc) * s;
+    Y = z > 0 ? 2.0 - s : s - 2.0;
+  }
+  const double p = X + Y, m = X - Y;
+  const int64_t P = (int64_t)std::floor(0.5 * (p + 1.0));
+  const int64_t M = (int64_t)std::floor(0.5 * (m + 1.0));
+  int64_t face, yc;  // yc: the face centre's Y
+  if (P == M) {
+    face = 4 + ((P % 4) + 4) % 4;
+    yc = 0;
+  } else if (P == M + 1) {
+    face = ((M % 4) + 4) % 4;
+    yc = 1;
+  } else {
+    face = 8 + ((P % 4) + 4) % 4;
+    yc = -1;
+  }
+  // position in the face: a along p, b along -m, both in [0, 1]
+  const double a = 0.5 * (p - (double)(2 * P - 1));
+  const double b = 0.5 * ((double)(2 * M + 1) - m);
+  int64_t ix = (int64_t)std::floor(a * (double)N), iy = (int64_t)std::floor(b * (double)N);
+  ix = std::min<int64_t>(std::max<int64_t>(ix, 0), N - 1);
+  iy = std::min<int64_t>(std::max<int64_t>(iy, 0), N - 1);
+  if (nest) {
     int64_t pix = 0;
-    for (int b2 = 0; b2 < 31; ++b2) pix |= (((ix >> b2) & 1) << (2 * b2)) | (((iy >> b2) & 1) << (2 * b2 + 1));
+    for (int bit = 0; bit < 31; ++bit)
+      pix |= (((ix >> bit) & 1) << (2 * bit)) | (((iy >> bit) & 1) << (2 * bit + 1));
     return face * N * N + pix;
   }
-  int64_t q = (int64_t)t;
-  if (q > 3) q = 3;
-  double tp = t - (double)q;
-  double sc = N * std::sqrt(3.0 * (1.0 - za));
-  int64_t jp = (int64_t)(tp * sc), jm = (int64_t)((1.0 - tp) * sc);
-  if (!nest) {
-    int64_t ir = jp + jm + 1;                       // ring counted from the nearer pole
-    int64_t ip = (int64_t)(t * ir);
-    ip = ((ip % (4 * ir)) + 4 * ir) % (4 * ir);
-    return z > 0 ? 2 * ir * (ir - 1) + ip : npix - 2 * ir * (ir + 1) + ip;
+  // RING: ring i (1 .. 4N - 1 from the north pole) and the place j (1 .. pixels in the ring) of the
+  // pixel centre X = X_f + (ix - iy) / N along it; X_f = the face centre's X
+  const int64_t xf = face < 4 ? 2 * face + 1 : face < 8 ? 2 * (face - 4) : 2 * (face - 8) + 1;
+  const int64_t i = (3 - yc) * N - ix - iy - 1;
+  int64_t nr, before, shift;
+  if (i < N) {                 // northern cap: 4 i pixels, centres at X = (2 j - 1) / i
+    nr = i;
+    before = 2 * i * (i - 1);
+    shift = 0;
+  } else if (i > 3 * N) {      // southern cap
+    nr = 4 * N - i;
+    before = 12 * N * N - 2 * nr * (nr + 1);
+    shift = 0;
+  } else {                     // equatorial rings: 4 N pixels, every other ring offset by half a pixel
+    nr = N;
+    before = 2 * N * (N - 1) + (i - N) * 4 * N;
+    shift = (i - N) & 1;
   }
-  if (jp > N - 1) jp = N - 1;
-  if (jm > N - 1) jm = N - 1;
-  int64_t face, ix, iy;
-  if (z > 0) { face = q; ix = N - jm - 1; iy = N - jp - 1; }
-  else { face = q + 8; ix = jp; iy = jm; }
-  int64_t pix = 0;
-  for (int b2 = 0; b2 < 31; ++b2) pix |= (((ix >> b2) & 1) << (2 * b2)) | (((iy >> b2) & 1) << (2 * b2 + 1));
-  return face * N * N + pix;
+  int64_t j = (xf * nr + ix - iy + 1 + shift) / 2;
+  if (j > 4 * nr) j -= 4 * nr;
+  if (j < 1) j += 4 * nr;
+  return before + j - 1;
 }
 
 // HEALPix pixels of n directions ([3][n]); nest: 1 NESTED, 0 RING.
@@ -733,7 +762,7 @@ int orc_trace(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n
   return trace_rays_impl(g, lv, bg, bg_n, p, dirs, n_rays, nullptr, o, n_threads);
 }
 
-// Rays stopped at the comoving distances chi_stop[i] (the geodesic finder's iso-chi surface, Sect. 2.6).
+// Rays stopped at the comoving distances chi_stop[i] (the geodesic finder's iso-chi surface, Sect. 2.5).
 int orc_trace_to_chi(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n, const orc_params* p,
                      const double* dirs, int64_t n_rays, const double* chi_stop, orc_out* o, int n_threads) {
   return trace_rays_impl(g, lv, bg, bg_n, p, dirs, n_rays, chi_stop, o, n_threads);

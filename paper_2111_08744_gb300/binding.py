@@ -81,6 +81,9 @@ def load():
         lib.mt_trace_rays_adjoint.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64,
                                               ctypes.POINTER(mt_ray_out), P, P, P, ctypes.POINTER(P),
                                               ctypes.c_int32, P]
+        lib.mt_trace_rays_jvp.restype = ctypes.c_int
+        lib.mt_trace_rays_jvp.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64,
+                                          ctypes.POINTER(mt_ray_out), ctypes.POINTER(P), P, P]
         lib.mt_trace_rays_lensing.restype = ctypes.c_int
         lib.mt_trace_rays_lensing.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64,
                                               ctypes.POINTER(mt_ray_out), P, P, P]
@@ -109,6 +112,8 @@ def load():
         lib.mt_status_str.argtypes = [ctypes.c_int]
         lib.mt_octree_info.restype = ctypes.c_int
         lib.mt_octree_info.argtypes = [P, P, P]
+        lib.mt_probe_fp64_fma_rate.restype = ctypes.c_int
+        lib.mt_probe_fp64_fma_rate.argtypes = [ctypes.c_int64, ctypes.c_int32, P, P]
         _lib = lib
         return lib
 
@@ -360,6 +365,30 @@ def trace_rays_adjoint(tree: Octree, params: TraceParams, dirs, jacobian=True, l
     return res
 
 
+def mt_trace_rays_jvp(tree, params, dirs, n_rays, out, d_rec, dxi, stream):
+    return load().mt_trace_rays_jvp(tree, params, dirs, n_rays, out, d_rec, dxi, stream)
+
+
+def trace_rays_jvp(tree: Octree, params: TraceParams, dirs, d_rec, out=None, stream=None):
+    """mt_trace_rays_jvp on CUDA tensors: the ray outputs plus "dxi" [3, N], the derivative of
+    the end points on the stop surface along the record perturbation d_rec (one float64 tensor
+    per level shaped like its records [count, n_slices, 4], or None for zero)."""
+    torch = _require_cuda()
+    n = int(dirs.shape[1])
+    if out is None:
+        out = alloc_outputs(n, dirs.device)
+    dxi = torch.empty((3, n), dtype=torch.float64, device=dirs.device)
+    keep = [t.contiguous() if t is not None else None for t in d_rec]
+    arr = (ctypes.c_void_p * len(keep))(*[t.data_ptr() if (t is not None and t.numel()) else None for t in keep])
+    o = ray_out_struct(out)
+    code = load().mt_trace_rays_jvp(tree.handle, ctypes.byref(params.c), dirs.data_ptr(), n, ctypes.byref(o), arr,
+                                    dxi.data_ptr(), _stream_handle(stream))
+    _check(code, "mt_trace_rays_jvp")
+    res = dict(out)
+    res["dxi"] = dxi
+    return res
+
+
 def trace_rays_lensing(tree: Octree, params: TraceParams, dirs, out=None, stream=None):
     """mt_trace_rays_lensing on CUDA tensors: the ray outputs plus the infinitesimal-beam
     distortion matrix "jac" [4, N] and "lens" [5, N] (Eq. 12; Born approximation when the
@@ -474,3 +503,16 @@ def pullback_coarse_phi(tree: Octree, dL_drec, slice_weight, n_coarse, stream=No
     _check(load().mt_pullback_coarse_phi(tree.handle, arr, w.ctypes.data_as(ctypes.c_void_p), out.data_ptr(),
                                          _stream_handle(stream)), "mt_pullback_coarse_phi")
     return out
+
+
+def mt_probe_fp64_fma_rate(iters, repeats, fma_per_s, stream):
+    return load().mt_probe_fp64_fma_rate(iters, repeats, fma_per_s, stream)
+
+
+def probe_fp64_fma_rate(iters: int = 1 << 14, repeats: int = 3, stream=None) -> float:
+    """Measured FP64 FMA lane-operations per second of the current device (calibration kernel)."""
+    _require_cuda()
+    v = ctypes.c_double(0.0)
+    _check(mt_probe_fp64_fma_rate(int(iters), int(repeats), ctypes.byref(v), _stream_handle(stream)),
+           "mt_probe_fp64_fma_rate")
+    return float(v.value)

@@ -3,8 +3,9 @@
 // potential records (every level, slice and component), by the exact adjoint of the
 // discrete ray map (RK4 of Eqs. 2-4 with CIC interpolation and level fallback, Sect. 2.2).
 //
+// FP64 octrees (FP32 octrees: mt_adjoint_mixed.cu, the adjoint of the mixed-precision step).
 // Per ray (one thread):
-//   1. integrate forward (FP64 arithmetic, T-precision records), keeping the state every
+//   1. integrate forward (FP64 arithmetic), keeping the state every
 //      `checkpoint_every` steps in a global checkpoint buffer;
 //   2. from the cotangent dL/dxi of the end point on the iso-eta surface,
 //      xi = x - (k/k0)(eta - eta_stop), form the cotangent of the final state;
@@ -395,18 +396,7 @@ cudaError_t launch_adjoint(const mt_octree* tree, const DevCones& C, const doubl
                                                                                             d_steps, tree->ws);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  std::vector<int> hs(n);
-  e = cudaMemcpyAsync(hs.data(), d_steps, sizeof(int) * n, cudaMemcpyDeviceToHost, stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-  if (e != cudaSuccess) return e;
-  std::vector<long long> off(n + 1);
-  off[0] = 0;
-  for (long long i = 0; i < n; ++i) off[i + 1] = off[i] + std::max(1, (hs[i] + seg_len - 1) / seg_len) + 1;
-  e = cudaMalloc(d_off_out, sizeof(long long) * (n + 1));
-  if (e != cudaSuccess) return e;
-  e = cudaMalloc(d_ck_out, sizeof(double) * 8 * (size_t)off[n]);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpy(*d_off_out, off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice);
+  e = adjoint_checkpoint_layout(d_steps, n, seg_len, d_off_out, d_ck_out, stream);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(tree->ws, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
@@ -421,10 +411,32 @@ cudaError_t launch_adjoint(const mt_octree* tree, const DevCones& C, const doubl
 
 }  // namespace
 
+// Checkpoint layout of a reverse sweep from the per-ray step counts d_steps [n] (device): ray i
+// gets ceil(steps_i / seg_len) + 1 slots of 8 doubles at slot offset (*d_off)[i].  Waits for
+// `stream`; allocates *d_off ([n + 1] offsets) and *d_ck (the checkpoints), which the caller frees.
+cudaError_t adjoint_checkpoint_layout(const int* d_steps, long long n, int seg_len, long long** d_off, double** d_ck,
+                                      cudaStream_t stream) {
+  std::vector<int> hs(n);
+  cudaError_t e = cudaMemcpyAsync(hs.data(), d_steps, sizeof(int) * n, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return e;
+  std::vector<long long> off(n + 1);
+  off[0] = 0;
+  for (long long i = 0; i < n; ++i) off[i + 1] = off[i] + std::max(1, (hs[i] + seg_len - 1) / seg_len) + 1;
+  e = cudaMalloc(d_off, sizeof(long long) * (n + 1));
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(d_ck, sizeof(double) * 8 * (size_t)off[n]);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*d_off, off.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice);
+}
+
 mt_status run_adjoint(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O,
                       const double* dL_dxi, double* const* dL_drec, int checkpoint_every, const TraceArgs& A,
                       cudaStream_t stream) {
   if (checkpoint_every < 1 || checkpoint_every > kMaxSegment) return MT_ERR_INVALID_ARG;
+  // FP32 octrees: the adjoint of the mixed-precision step the trace integrates there
+  if (tree->precision != MT_FIELD_FP64)
+    return run_adjoint_mixed(tree, C, dirs, O, dL_dxi, dL_drec, checkpoint_every, A, stream);
   RecBar R;
   for (int l = 0; l <= kMaxLevels; ++l) R.lv[l] = (l <= tree->n_levels) ? dL_drec[l] : nullptr;
   int* d_steps = nullptr;
@@ -432,10 +444,7 @@ mt_status run_adjoint(const mt_octree* tree, const DevCones& C, const double* di
   double* d_ck = nullptr;
   cudaError_t e = cudaMalloc(&d_steps, sizeof(int) * std::max<long long>(1, A.n_rays));
   if (e == cudaSuccess) {
-    if (tree->precision == MT_FIELD_FP64)
-      e = launch_adjoint<double>(tree, C, dirs, O, A, dL_dxi, R, checkpoint_every, d_steps, &d_off, &d_ck, stream);
-    else
-      e = launch_adjoint<float>(tree, C, dirs, O, A, dL_dxi, R, checkpoint_every, d_steps, &d_off, &d_ck, stream);
+    e = launch_adjoint<double>(tree, C, dirs, O, A, dL_dxi, R, checkpoint_every, d_steps, &d_off, &d_ck, stream);
   }
   cudaError_t e2 = cudaStreamSynchronize(stream);
   if (d_steps) cudaFree(d_steps);

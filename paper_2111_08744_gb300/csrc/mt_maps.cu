@@ -1,4 +1,4 @@
-// HEALPix maps of per-ray quantities (Sect. 2.5) and the deflection angle alpha = theta - beta.
+// HEALPix maps of per-ray quantities (Sect. 2.4) and the deflection angle alpha = theta - beta.
 //
 // Rays shot at pixel centres give maps directly (ray i = pixel i); rays at other directions (a
 // finer resolution, a geodesic finder's solutions) are binned: each direction is assigned its

@@ -63,8 +63,9 @@ __device__ __forceinline__ bool stage_coords(const DevField& F, const int* ib, c
 // RK4 stages of a ray stay in one neighbourhood most of the time (a step moves 1/N of a cell), so
 // most stages read their records from shared memory instead of L1/L2, and skip the index work.
 struct LaneCache {
-  float4* rec;   // rec[j * stride] for j = 0..15 (corner-major, lanes interleaved: no bank conflicts)
-  int4* key;     // (level << 8 | slice, i0x, i0y, i0z); level -1: empty
+  float4* rec;   // rec[j * stride] for j = 0..15 (corner-major, lanes interleaved: no bank conflicts);
+                 // the TSC instances keep the 27 neighbour rows here instead (tsc_gather_cached)
+  int4* key;     // (level << 8 | slice, i0x, i0y, i0z) (TSC: the cell, not the lower corner); level -1: empty
   int stride;
   int4* loc;     // last locate answer: the cell (x, y, z) of level w that contains the point, w the
                  // finest level there (w = -1: empty); a property of the field, valid across rays;
@@ -74,10 +75,12 @@ struct LaneCache {
 // CIC at level l (FP32) from finest-level integer coordinates; v as in cic_gather.  With
 // WithD, dv[d][q] also receives the derivative of the interpolant of component q with respect
 // to the level-l cell coordinate d (the weights' derivatives, +-1 times the other two weights).
+// i0_out, f_out (if non-null) receive the lower corner and the in-cell fractions of the neighbourhood.
 template <bool WithD = false>
 __device__ __forceinline__ bool cic_int_cached(const DevField& F, int l, const int* ic, const float* fc, int s,
                                                float* v, unsigned* err, const LaneCache& lc,
-                                               float (*dv)[8] = nullptr) {
+                                               float (*dv)[8] = nullptr, int* i0_out = nullptr,
+                                               float* f_out = nullptr) {
   const int sh = F.L - l;
   const float inv = 1.0f / (float)(1 << sh);
   int i0[3];
@@ -92,6 +95,13 @@ __device__ __forceinline__ bool cic_int_cached(const DevField& F, int l, const i
     } else {
       i0[d] = ilev - 1;
       f[d] = fl + 0.5f;
+    }
+  }
+  if (i0_out) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      i0_out[d] = i0[d];
+      f_out[d] = f[d];
     }
   }
   const int4 key = make_int4((l << 8) | s, i0[0], i0[1], i0[2]);
@@ -169,12 +179,76 @@ __device__ __forceinline__ bool cic_int(const DevField& F, int l, const int* ic,
   return cic_gather<float>(F, l, i0, f, s, v, err);
 }
 
+// TSC (Eq. 9) at level l around cell c with the lane's neighbour cache: the rows of the 27 cells
+// around c (the same for every position inside c) are kept in the lane cache's record area, keyed by
+// (level, slice bracket, c), and reused while the photon stays in that cell, so the octet probes and
+// the Morton arithmetic run only when it enters another cell (the neighbour caching of the paper's
+// TSC mode, Sect. 2.2); the 27 x 2 records are read at every stage.  v, dout as tsc_gather.
+template <bool WithD>
+__device__ __forceinline__ bool tsc_gather_cached(const DevField& F, int l, const long long* c, const float* t, int s,
+                                                  float* out, unsigned* err, const LaneCache& lc,
+                                                  float (*dout)[8] = nullptr) {
+  unsigned* rows = reinterpret_cast<unsigned*>(lc.rec);  // rows[m * stride], m = mx + 3 my + 9 mz
+  const int4 key = make_int4((l << 8) | s, (int)c[0], (int)c[1], (int)c[2]);
+  const int4 old = *lc.key;
+  if (!(old.x == key.x && old.y == key.y && old.z == key.z && old.w == key.w)) {
+    unsigned a[3][3], plo[3], oct[8];
+    if (!tsc_octets(F, l, c, a, plo, oct, err)) return false;
+#pragma unroll 1
+    for (int mz = 0; mz < 3; ++mz)
+#pragma unroll 1
+      for (int my = 0; my < 3; ++my)
+#pragma unroll
+        for (int mx = 0; mx < 3; ++mx) rows[(mx + 3 * my + 9 * mz) * lc.stride] = tsc_row(l, a, plo, oct, mx, my, mz);
+    *lc.key = key;
+  }
+  float w[3][3], dw[3][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) tsc_weights<float>(t[d], w[d], WithD ? dw[d] : nullptr);
+  const float4* rec = (const float4*)F.rec[l];
+  const int S = F.S;
+  const int s1 = (S > 1) ? s + 1 : s;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) out[q] = 0.0f;
+  if constexpr (WithD) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) dout[0][q] = dout[1][q] = dout[2][q] = 0.0f;
+  }
+#pragma unroll 1
+  for (int mz = 0; mz < 3; ++mz) {
+#pragma unroll 1
+    for (int my = 0; my < 3; ++my) {
+#pragma unroll
+      for (int mx = 0; mx < 3; ++mx) {
+        const float4* rc = rec + (size_t)rows[(mx + 3 * my + 9 * mz) * lc.stride] * (size_t)S;
+        const float4 r0 = __ldg(rc + s), r1 = __ldg(rc + s1);
+        const float rr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+        const float wyz = w[1][my] * w[2][mz];
+        const float wgt = w[0][mx] * wyz;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) out[q] += wgt * rr[q];
+        if constexpr (WithD) {
+          const float d0 = dw[0][mx] * wyz, d1 = w[0][mx] * dw[1][my] * w[2][mz], d2 = w[0][mx] * w[1][my] * dw[2][mz];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            dout[0][q] += d0 * rr[q];
+            dout[1][q] += d1 * rr[q];
+            dout[2][q] += d2 * rr[q];
+          }
+        }
+      }
+    }
+  }
+  return true;
+}
+
 // NGP or TSC (Eqs. 7, 9) at level l (FP32) from finest-level integer coordinates: the level-l
 // cell is ic >> (L - l) and t the position in it relative to its centre; v (and dv with WithD)
-// as in cic_int_cached.  No lane cache: the 27 TSC cells are gathered every stage.
+// as in cic_int_cached.  TSC with a lane cache keeps the cell's 27 neighbour rows
+// (tsc_gather_cached).
 template <bool WithD, int IP>
 __device__ __forceinline__ bool interp_int(const DevField& F, int l, const int* ic, const float* fc, int s, float* v,
-                                           unsigned* err, float (*dv)[8] = nullptr) {
+                                           unsigned* err, float (*dv)[8] = nullptr, const LaneCache* lc = nullptr) {
   const int sh = F.L - l;
   const float inv = 1.0f / (float)(1 << sh);
   long long c[3];
@@ -191,6 +265,7 @@ __device__ __forceinline__ bool interp_int(const DevField& F, int l, const int* 
     }
     return ngp_gather<float>(F, l, c, s, v, err);
   }
+  if (lc) return tsc_gather_cached<WithD>(F, l, c, t, s, v, err, *lc, WithD ? dv : nullptr);
   return tsc_gather<float>(F, l, c, t, s, v, err, WithD ? dv : nullptr);
 }
 
@@ -244,6 +319,12 @@ struct StageF {
   float G[3][3];  // G[i][d] = d g_i / d x_d (derivative of the trilinear interpolant)
   float ge[3];    // d g_i / d eta (slope between the bracketing slices)
   float dpe[3];   // d phi_eta / d x_d
+  // the CIC neighbourhood the stage interpolated from (CIC only): level, slice bracket, lower
+  // corner, in-cell fractions, slice weight and 1 / (eta_{s+1} - eta_s) (0 with one slice)
+  int lev, sl;
+  int i0[3];
+  float f[3];
+  float wt, ids;
 };
 
 // FP32 right-hand side of Eqs. (2)-(4) at the stage with offsets (offx, offe) from the step
@@ -307,10 +388,10 @@ __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const Mi
       int l = lfin;
       if constexpr (IP != MT_INTERP_CIC) {
         for (; l >= 0; --l)
-          if (interp_int<WithD, IP>(F, l, ic, fc, s, v, err, WithD ? dv : nullptr)) break;
+          if (interp_int<WithD, IP>(F, l, ic, fc, s, v, err, WithD ? dv : nullptr, lc)) break;
       } else if constexpr (WithD) {
         for (; l >= 0; --l)
-          if (cic_int_cached<true>(F, l, ic, fc, s, v, err, *lc, dv)) break;
+          if (cic_int_cached<true>(F, l, ic, fc, s, v, err, *lc, dv, sf->i0, sf->f)) break;
       } else if (lc) {
         for (; l >= 0; --l)
           if (cic_int_cached(F, l, ic, fc, s, v, err, *lc)) break;
@@ -334,6 +415,10 @@ __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const Mi
         pe = (v[4] - v[0]) * ids;
       }
       if constexpr (WithD) {
+        sf->lev = l;
+        sf->sl = s;
+        sf->wt = F.S > 1 ? (es + offe) * F.inv_dseta[s] : 0.0f;
+        sf->ids = F.S > 1 ? F.inv_dseta[s] : 0.0f;
         const float inv = F.inv_dxf_f / (float)(1 << (F.L - l));  // d (level-l cell coordinate) / d x
         if (F.S == 1) {
 #pragma unroll

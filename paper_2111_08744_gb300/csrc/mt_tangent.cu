@@ -525,7 +525,7 @@ void launch_tangent_scheme(const mt_octree* tree, const DevCones& C, const doubl
 
 // ----------------------------------------------------------------------------- geodesic finder
 
-// Geodesic finder (Sect. 2.6, Eq. 22): the observed direction theta whose ray, stopped on the sphere
+// Geodesic finder (Sect. 2.5, Eq. 22): the observed direction theta whose ray, stopped on the sphere
 // |x - x_o| = chi_s of the source, is seen from the observer in the source's direction beta.
 // Newton on the screen (e_1, e_2) of theta_i:  theta_{i+1} = theta_i - A^{-1} (beta_i - beta), with
 // A = d beta / d theta the exact derivative of the discrete map (the forward tangents, projected

@@ -340,6 +340,11 @@ mt_status check_trace_params(const mt_trace_params* p, int64_t n_rays);
 void fill_cones(const mt_octree* tree, const mt_trace_params* params, DevCones* C);
 cudaError_t launch_tangent(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O, double* jac,
                            double* lens, const TraceArgs& A, cudaStream_t stream);
+mt_status run_adjoint_mixed(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O,
+                            const double* dL_dxi, double* const* dL_drec, int checkpoint_every, const TraceArgs& A,
+                            cudaStream_t stream);
+cudaError_t adjoint_checkpoint_layout(const int* d_steps, long long n, int seg_len, long long** d_off, double** d_ck,
+                                      cudaStream_t stream);
 mt_status run_adjoint(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O,
                       const double* dL_dxi, double* const* dL_drec, int checkpoint_every, const TraceArgs& A,
                       cudaStream_t stream);

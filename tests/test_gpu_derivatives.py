@@ -188,8 +188,40 @@ def _loss_and_xi(w, out):
     return float(((xi - ref) ** 2).sum()), xi - ref
 
 
+def _near_path_rows(w, lev, radius_cells, seed, count):
+    """Seeded rows of level `lev` whose cells lie within radius_cells (max norm, periodic) of some
+    ray's straight path to the stop distance: records a ray can use (chosen from the geometry alone)."""
+    es = oracle.eta_stop(w.bg, float(w.z_max[0]))
+    chi = (w.bg[-1, 0] - es) * 1.01
+    dxl = w.box / (w.n_coarse << lev)
+    ci, cj, ck = I._demorton(w.levels[lev].keys)
+    xc = (np.stack([ci, cj, ck]).astype(np.float64) + 0.5) * dxl
+    s = np.arange(0.0, chi + dxl, 0.5 * dxl)
+    pts = (w.observer[0][:, None, None] + w.dirs[:, :, None] * s[None, None, :]).reshape(3, -1) % w.box
+    near = np.zeros(xc.shape[1], bool)
+    for a in range(0, pts.shape[1], 4096):
+        q = (xc[:, :, None] - pts[:, None, a:a + 4096] + 0.5 * w.box) % w.box - 0.5 * w.box
+        near |= (np.abs(q).max(axis=0) < radius_cells * dxl).any(axis=1)
+    rows = np.nonzero(near)[0]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.choice(rows, size=min(count, rows.size), replace=False)
+
+
+def _richardson_fd(loss, d):
+    """Central differences at d and d/2 combined to cancel the d^2 term; also whether both pairs
+    took the same step counts (no decision crossed) and the two quotients."""
+    q = []
+    same = True
+    for dd in (d, 0.5 * d):
+        (lp, sp), (lm, sm) = loss(+dd), loss(-dd)
+        q.append((lp - lm) / (2 * dd))
+        same = same and np.array_equal(sp, sm)
+    return (4.0 * q[1] - q[0]) / 3.0, same, q
+
+
 def test_adjoint_matches_oracle_finite_differences():
-    """dL/d(record) for L = sum |xi - xi_FLRW|^2 against central differences of the oracle."""
+    """dL/d(record) for L = sum |xi - xi_FLRW|^2 against central differences of the oracle, on
+    seeded records (each level, component and slice) of cells the rays pass."""
     import dataclasses
     import torch
     w = _adj_workload()
@@ -198,43 +230,36 @@ def test_adjoint_matches_oracle_finite_differences():
     r = _gpu(w, jacobian=False, lensing=False, dL_dxi=torch.from_numpy(2.0 * dxi).cuda())
     grads = r["dL_drec"]
     assert all(np.isfinite(g).all() for g in grads)
-    # the records with the largest gradient components, per level and component type
     picks = []
-    for lev, g in enumerate(grads):
-        for comp in range(4):
-            flat = np.abs(g[:, :, comp]).ravel()
-            if flat.max() == 0:
-                continue
-            i = int(np.argmax(flat))
-            picks.append((lev, i // g.shape[1], i % g.shape[1], comp))
-    assert len(picks) >= 6
+    for lev in range(len(w.levels)):
+        for i, row in enumerate(_near_path_rows(w, lev, 1.0, 100 + lev, 8)):
+            picks.append((lev, int(row), i % w.n_slices, i % 4))
     errs, kinked = [], []
+    gscale = max(np.abs(g).max() for g in grads)
     for lev, row, sl, comp in picks:
         val = w.levels[lev].records[row, sl, comp]
         g = grads[lev][row, sl, comp]
-        fds = []
-        for rel in (1e-2, 1e-3):
-            d = rel * max(abs(val), 1e-7 if comp == 0 else 1e-9)
-            Ls, steps = [], []
-            for sgn in (+1, -1):
-                lv = [I.Level(l.keys, l.records.copy()) for l in w.levels]
-                lv[lev].records[row, sl, comp] = val + sgn * d
-                o = oracle.trace(dataclasses.replace(w, levels=lv))
-                Ls.append(_loss_and_xi(w, o)[0])
-                steps.append(o["n_steps"])
-            fds.append(((Ls[0] - Ls[1]) / (2 * d), np.array_equal(steps[0], steps[1])))
-        (fd1, same1), (fd2, same2) = fds
-        # a perturbation that moves a ray across a cell-face or level decision makes L kink:
-        # the two difference quotients then disagree; such picks are reported, not judged
-        if not (same1 and same2) or abs(fd1 - fd2) > 1e-4 * max(abs(fd1), 1e-30):
-            kinked.append((lev, row, sl, comp, fd1, fd2, g))
+        rms = np.sqrt((w.levels[lev].records[:, :, comp] ** 2).mean())
+
+        def loss(t):
+            lv = [I.Level(l.keys, l.records.copy()) for l in w.levels]
+            lv[lev].records[row, sl, comp] = val + t
+            o = oracle.trace(dataclasses.replace(w, levels=lv))
+            return _loss_and_xi(w, o)[0], o["n_steps"]
+
+        fd, same, q = _richardson_fd(loss, 0.02 * rms)
+        floor = 1e-6 * gscale
+        # a perturbation that moves a ray across a decision (a step count, a level, or a CIC cell plane
+        # where the interpolant's derivative jumps) between the two step sizes makes the quotients
+        # disagree: such picks are reported, not judged, and must be few
+        if not same or abs(q[0] - q[1]) > 1e-5 * max(abs(fd), floor):
+            kinked.append((lev, row, sl, comp, q, g))
             continue
-        errs.append(abs(fd1 - g) / max(abs(fd1), 1e-30))
+        errs.append(abs(fd - g) / max(abs(fd), floor))
     errs = np.array(errs)
     print("relative errors", errs, "kinked", kinked)
-    assert len(errs) >= 6, kinked
-    assert np.median(errs) < 1e-5, errs
-    assert errs.max() < 1e-4, errs
+    assert len(kinked) <= len(picks) // 8, kinked
+    assert errs.max() < 1e-5, errs
 
 
 def test_adjoint_checkpoint_interval_does_not_change_gradients():
@@ -250,7 +275,7 @@ def test_adjoint_checkpoint_interval_does_not_change_gradients():
 
 def test_pullback_to_coarse_phi_matches_oracle_finite_differences():
     """dL/dphi_0 through the field model (records rebuilt from phi_0 by the generator) against
-    central differences of the oracle's loss in individual coarse cells."""
+    central differences of the oracle's loss in seeded coarse cells the rays pass."""
     import dataclasses
     import torch
     from paper_2111_08744_gb300 import binding as B
@@ -263,32 +288,28 @@ def test_pullback_to_coarse_phi_matches_oracle_finite_differences():
                                dL_dxi=torch.from_numpy(2 * dxi).cuda())
     g = B.pullback_coarse_phi(tree, res["dL_drec"], w.slice_weight, w.n_coarse).cpu().numpy()
     tree.free()
-    n = w.n_coarse
-    order = np.argsort(-np.abs(g))[:10]
     errs, kinked = [], []
-    for m in order:
+    rows = _near_path_rows(w, 0, 1.0, 7, 16)
+    for m in rows:
         ci, cj, ck = I._demorton(np.array([m], dtype=np.uint64))
         i, j, k = int(ci[0]), int(cj[0]), int(ck[0])
-        fds = []
-        for rel in (1e-2, 1e-3):
-            d = rel * 1e-5
-            Ls, steps = [], []
-            for sgn in (+1, -1):
-                phi = w.phi0.copy()
-                phi[i, j, k] += sgn * d
-                o = oracle.trace(dataclasses.replace(w, levels=I.records_from_phi0(w, phi)))
-                Ls.append(_loss_and_xi(w, o)[0])
-                steps.append(o["n_steps"])
-            fds.append(((Ls[0] - Ls[1]) / (2 * d), np.array_equal(steps[0], steps[1])))
-        (f1, s1), (f2, s2) = fds
-        if not (s1 and s2) or abs(f1 - f2) > 1e-4 * abs(f1):
-            kinked.append((m, f1, f2, g[m]))
+
+        def loss(t):
+            phi = w.phi0.copy()
+            phi[i, j, k] += t
+            o = oracle.trace(dataclasses.replace(w, levels=I.records_from_phi0(w, phi)))
+            return _loss_and_xi(w, o)[0], o["n_steps"]
+
+        fd, same, q = _richardson_fd(loss, 2e-7)
+        floor = 1e-6 * np.abs(g).max()
+        if not same or abs(q[0] - q[1]) > 1e-5 * max(abs(fd), floor):
+            kinked.append((m, q, g[m]))
             continue
-        errs.append(abs(f1 - g[m]) / abs(f1))
+        errs.append(abs(fd - g[m]) / max(abs(fd), floor))
     errs = np.array(errs)
     print("pullback relative errors", errs, "kinked", kinked)
-    assert len(errs) >= 6, kinked
-    assert np.median(errs) < 1e-5 and errs.max() < 1e-4, errs
+    assert len(kinked) <= len(rows) // 8, kinked
+    assert errs.max() < 1e-5, errs
 
 
 def test_autograd_functions_backpropagate_the_adjoint():

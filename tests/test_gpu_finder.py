@@ -1,4 +1,4 @@
-"""Geodesic finder on the GPU (mt_find_geodesics, Sect. 2.6, Eq. 22), checked against its defining
+"""Geodesic finder on the GPU (mt_find_geodesics, Sect. 2.5, Eq. 22), checked against its defining
 equation with the oracle: the oracle traces each found direction to the source's sphere (its own
 iso-chi stop) and must see the source in its direction."""
 import functools

@@ -1,4 +1,4 @@
-"""HEALPix maps on the GPU (mt_healpix_bin) and the deflection angle (mt_deflection), Sect. 2.5:
+"""HEALPix maps on the GPU (mt_healpix_bin) and the deflection angle (mt_deflection), Sect. 2.4:
 pixels against the oracle's assignment, binned maps against the NESTED hierarchy, and alpha
 against its definition on oracle-traced end points."""
 import numpy as np

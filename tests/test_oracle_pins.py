@@ -401,7 +401,7 @@ def test_step_size_follows_refinement_level():
     np.testing.assert_allclose(d2, d0, rtol=1e-11)
 
 
-# ---------------------------------------------------------------- iso-chi stop (Sect. 2.6 geodesic finder)
+# ---------------------------------------------------------------- iso-chi stop (Sect. 2.5 geodesic finder)
 
 def test_iso_chi_stop_flrw_and_constant_gradient():
     """FLRW: the ray ends exactly on the sphere along its direction; phi = g.x: the end point on
