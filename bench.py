@@ -357,6 +357,9 @@ def run_ours(args, ws, rank):
         v, ns, threads, dt = oracle_sample(w, budget_s=args.ref_budget, interp=args.interp)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{ns} seeded rays of the 786,432 ({dt:.1f} s of FP64 oracle work on {threads} threads)"}
+    extras = None
+    if rank == 0 and ws == 1 and not args.no_extras and args.rays == 0 and args.interp == "cic":
+        extras = run_extras(w, tree, dev)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64 state / f32 field", "data": "synthetic", "config": dict(workload_config(w), interp=args.interp),
@@ -364,9 +367,104 @@ def run_ours(args, ws, rank):
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": args.steps, "clocks": ck, "step_ms_all": times, "wall_s_timed": wall}
+    if extras is not None:
+        line["extras"] = extras
     if rank == 0:
         print(json.dumps(line), flush=True)
     tree.free()
+
+
+def run_extras(w, tree, dev):
+    """Short, reduced-size passes of the other configurations, reported beside the headline so that
+    they are measured in the same run (each with its own clock record):
+      * batched: the 64 light cones of the batched configuration at 1/16 of their ray counts in one
+        persistent launch (graph replay) against one launch per cone;
+      * fp64_field: the FP64-field form on a seeded 1/16 of the benchmark rays, and the largest
+        relative difference of the mixed form's outputs from it;
+      * differentiation: 256 x 256 rays of the differentiation workload (128^3 + 3 levels, 10 x 10
+        deg to z = 1) on FP32 records: forward, distortion matrix (mixed tangent step) and the mixed
+        reverse sweep of the end-point loss (checkpoints every 64 steps)."""
+    import torch
+
+    from paper_2111_08744_gb300 import autotune as AT
+    from paper_2111_08744_gb300 import binding as B
+    from paper_2111_08744_gb300 import inputs as I
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        r = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return r, a.elapsed_time(b)
+
+    out = {}
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    # batched light cones (1/16 of the ray counts)
+    wb = I.batched_cones(w, n_cones=64, seed=4113, scale=1.0 / 16)
+    pb = B.TraceParams.from_workload(wb)
+    db = torch.from_numpy(wb.dirs).to(dev)
+    g = AT.TraceGraph(tree, pb, db)
+    g.replay()
+    _, ms_b = timed(g.replay)
+    steps_b = int(g.out["n_steps"].sum().item())
+    ob = B.alloc_outputs(wb.n_rays, dev)
+
+    def per_cone():
+        for c in range(wb.observer.shape[0]):
+            lo, hi = int(wb.ray_begin[c]), int(wb.ray_begin[c + 1])
+            if hi > lo:
+                p1 = B.TraceParams(wb.observer[c:c + 1], wb.z_max[c:c + 1], [0, hi - lo], wb.steps_per_cell,
+                                   max_steps=pb.c.max_steps)
+                B.trace_rays(tree, p1, db[:, lo:hi].contiguous(), {k: v[..., lo:hi] for k, v in ob.items()})
+
+    _, ms_u = timed(per_cone)
+    out["batched"] = {"workload": "64 light cones in the benchmark field, z_max 0.3-2, 1/16 of the ray counts",
+                      "n_rays": wb.n_rays, "n_cones": 64, "one_launch_ms": ms_b, "rays_per_s": wb.n_rays / (ms_b * 1e-3),
+                      "rk4_steps_per_s": steps_b / (ms_b * 1e-3), "one_launch_per_cone_ms": ms_u}
+    del g, ob
+    # FP64-field form on a seeded 1/16 of the benchmark rays
+    rng = np.random.Generator(np.random.PCG64(5))
+    idx = np.sort(rng.choice(w.n_rays, size=w.n_rays // 16, replace=False))
+    ws = I.with_rays(w, w.dirs[:, idx])
+    t64 = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, w.levels, w.bg, "fp64")
+    ps = B.TraceParams.from_workload(ws)
+    ds = torch.from_numpy(ws.dirs).to(dev)
+    o64, ms64 = timed(lambda: B.trace_rays(t64, ps, ds))
+    o32 = B.trace_rays(tree, ps, ds)
+    torch.cuda.synchronize()
+    err = {}
+    for k, fl in (("x", 1.0), ("chi", 1.0), ("z5", 1e-6), ("d_l", 1.0)):
+        r = o64[k].double()
+        err[k] = float(((o32[k].double() - r).abs() / r.abs().clamp_min(fl)).max().item())
+    steps64 = int(o64["n_steps"].sum().item())
+    out["fp64_field"] = {"workload": "the benchmark field with FP64 records, a seeded 1/16 of its rays",
+                         "n_rays": int(idx.size), "ms": ms64, "rays_per_s": idx.size / (ms64 * 1e-3),
+                         "rk4_steps_per_s": steps64 / (ms64 * 1e-3), "max_rel_diff_mixed_vs_fp64": err}
+    t64.free()
+    del o64, o32
+    # differentiation workload, 256 x 256 rays
+    wd = I.cached(I.config_diff, n_pix=256)
+    td = B.Octree(wd.box, wd.n_coarse, wd.periodic, wd.slice_eta, I.fp32_levels(wd), wd.bg, "fp32")
+    pd = B.TraceParams.from_workload(wd)
+    dd = torch.from_numpy(wd.dirs).to(dev)
+    ref = B.trace_rays(td, B.TraceParams.from_workload(wd, gravity_on=False), dd)["xi"]
+    B.trace_rays(td, pd, dd)
+    fwd, ms_f = timed(lambda: B.trace_rays(td, pd, dd))
+    _, ms_t = timed(lambda: B.trace_rays_adjoint(td, pd, dd, jacobian=True, lensing=True))
+    dxi = 2.0 * (fwd["xi"] - ref)
+    _, ms_r = timed(lambda: B.trace_rays_adjoint(td, pd, dd, jacobian=False, lensing=False, dL_dxi=dxi,
+                                                 checkpoint_every=64))
+    steps_d = int(fwd["n_steps"].sum().item())
+    td.free()
+    out["differentiation"] = {"workload": "differentiation field (128^3 + 3 levels), 256 x 256 rays over 10 x 10 deg "
+                                          "to z = 1, FP32 records", "n_rays": wd.n_rays, "forward_ms": ms_f,
+                              "distortion_matrix_ms": ms_t, "reverse_sweep_ms": ms_r,
+                              "reverse_over_forward": ms_r / ms_f, "forward_rk4_steps_per_s": steps_d / (ms_f * 1e-3),
+                              "reverse_rk4_steps_per_s": steps_d / (ms_r * 1e-3)}
+    out["clocks"] = clocks.stop()
+    return out
 
 
 def run_batched(args, ws, rank):
@@ -664,6 +762,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the reduced passes of the batched, FP64-field and differentiation configurations")
     ap.add_argument("--rays", type=int, default=0, help="trace a seeded subset of N rays (profiling only)")
     ap.add_argument("--workload", default="amr", choices=["amr", "batched", "large", "diff"],
                     help="amr: the headline benchmark; batched: 64 light cones (separate report)")

@@ -357,6 +357,20 @@ mt_status mt_pullback_coarse_phi(const mt_octree* tree, double* const* dL_drec, 
                                  double* dL_dphi0, void* stream);
 
 /*
+ * mt_field_from_coarse_phi -- the forward map of the field model of mt_pullback_coarse_phi: the
+ * records of every level from the coarse potential phi0 (device [N_0^3] FP64, Morton order), written
+ * to records[l] (device FP64 [count_l][n_slices][4], the octree's row order; overwritten):
+ *   records_0[c][s] = w_s (phi_0[c], (D phi_0)[c]) + base_0[c][s],
+ *   records_l[c][s] = w_s (I_0[phi_0](x_c), I_0[D phi_0](x_c)) + base_l[c][s],
+ * with D, I_0 and w_s as there; base[l] (device, same layout; NULL or a NULL entry: zero) holds the
+ * terms that do not depend on phi_0 (the records at phi_0 = 0).  The octree supplies the geometry
+ * (keys, counts), not its records.  Uses a temporary device buffer (4 doubles per coarse cell);
+ * synchronous.  Errors: MT_ERR_INVALID_ARG, MT_ERR_OOM, MT_ERR_CUDA.
+ */
+mt_status mt_field_from_coarse_phi(const mt_octree* tree, const double* phi0, const double* slice_weight,
+                                   const double* const* base, double* const* records, void* stream);
+
+/*
  * mt_trace_rays_noalloc -- the same trace as mt_trace_rays, for callers that must not
  * allocate GPU memory.  The paper has no counterpart: this is a property of this
  * library's interface, not of the method.
@@ -395,6 +409,15 @@ mt_status mt_trace_rays_noalloc(const mt_octree* tree, const mt_trace_params* pa
  * Errors: MT_ERR_INVALID_ARG.
  */
 mt_status mt_set_launch_config(mt_octree* tree, int32_t block_size, int32_t blocks_per_sm);
+
+/*
+ * mt_set_trace_options -- further tuning of mt_trace_rays on this octree (results do not depend on
+ * it): ray_chunk = ray ids a warp claims from the queue at a time (a multiple of 32 in [32, 1024];
+ * 0: default 32); staging (FP32 octrees, CIC) = 1: each ray's 8 CIC records of both slices are
+ * staged in shared memory and reused while the ray stays in that neighbourhood, 2: read through L1
+ * at every stage (no shared memory), 0: default (1).  Errors: MT_ERR_INVALID_ARG.
+ */
+mt_status mt_set_trace_options(mt_octree* tree, int32_t ray_chunk, int32_t staging);
 
 /*
  * mt_device_status -- synchronise `stream` and return the device-side flag of

@@ -4,8 +4,9 @@
 CUDA tensors [count, n_slices, 4]) to the rays' end points on their iso-eta stop surfaces,
 xi [3, N]; its backward runs mt_trace_rays_adjoint (reverse mode) on the GPU.
 `CoarsePhiEndpoints.apply(tc, phi0)` starts from the coarse potential phi0 [N, N, N]: the
-records are rebuilt by the workload's field model and the backward adds
-mt_pullback_coarse_phi.  Both integrate in FP64 arithmetic (the adjoint's forward map).
+records are rebuilt on the GPU by the field model (mt_field_from_coarse_phi, with the workload's
+phi0-independent detail terms computed once) and the backward adds mt_pullback_coarse_phi, its
+transpose.  Both integrate in FP64 arithmetic (the adjoint's forward map).
 """
 from __future__ import annotations
 
@@ -23,6 +24,29 @@ class TraceContext:
         self.params = B.TraceParams.from_workload(workload)
         self.dirs = torch.from_numpy(np.ascontiguousarray(workload.dirs)).cuda()
         self.checkpoint_every = checkpoint_every
+
+    def morton_index(self):
+        """key[i * N^2 + j * N + k] = Morton key of coarse cell (i, j, k) (CUDA int64)."""
+        if getattr(self, "_key", None) is None:
+            from . import inputs as I
+            n = self.w.n_coarse
+            ii, jj, kk = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+            self._key = torch.from_numpy(I.morton3(ii.ravel(), jj.ravel(), kk.ravel()).astype(np.int64)).cuda()
+        return self._key
+
+    def field_records(self, phi0):
+        """The records of every level from phi0 [N, N, N] (CUDA), by the field model on the GPU; the
+        terms that do not depend on phi0 (the workload's detail tiles) are computed once."""
+        from . import inputs as I
+        w = self.w
+        if getattr(self, "_base", None) is None:
+            zero = I.records_from_phi0(w, np.zeros((w.n_coarse,) * 3))
+            self._base = [torch.from_numpy(l.records).cuda() for l in zero]
+            self._geom = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, w.levels, w.bg, "fp64")
+        key = self.morton_index()
+        phi_m = torch.empty(key.numel(), dtype=torch.float64, device=key.device)
+        phi_m[key] = phi0.detach().to(torch.float64).reshape(-1)
+        return B.field_from_coarse_phi(self._geom, phi_m, w.slice_weight, base=self._base)
 
     def tree(self, records):
         w = self.w
@@ -72,22 +96,17 @@ class RayEndpoints(torch.autograd.Function):
 class CoarsePhiEndpoints(torch.autograd.Function):
     @staticmethod
     def forward(ctx, tc, phi0):
-        from . import inputs as I
-        lv = I.records_from_phi0(tc.w, phi0.detach().cpu().numpy().astype(np.float64))
-        recs = [torch.from_numpy(l.records).cuda() for l in lv]
+        recs = tc.field_records(phi0)
         ctx.tc = tc
         ctx.recs = recs
         return tc.endpoints(recs)
 
     @staticmethod
     def backward(ctx, grad_xi):
-        from . import inputs as I
         tc = ctx.tc
         tree, grads = tc.record_grads(ctx.recs, grad_xi)
         g = B.pullback_coarse_phi(tree, grads, tc.w.slice_weight, tc.w.n_coarse)
         torch.cuda.synchronize()
         tree.free()
         n = tc.w.n_coarse
-        ii, jj, kk = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
-        key = torch.from_numpy(I.morton3(ii.ravel(), jj.ravel(), kk.ravel()).astype(np.int64)).to(g.device)
-        return None, g[key].reshape(n, n, n)
+        return None, g[tc.morton_index()].reshape(n, n, n)

@@ -1,9 +1,10 @@
 """Launch-shape autotuner and CUDA-graph replay for the trace kernel.
 
 `autotune(tree, params, dirs)` times mt_trace_rays on a seeded sample of the rays for each
-candidate (threads per block, blocks per SM), keeps the fastest on the octree
-(mt_set_launch_config) and caches the choice in a JSON file keyed by the device name and a
-workload signature.  Results do not depend on the launch shape, only the time does.
+candidate (threads per block, blocks per SM, ray ids a warp claims per refill, staging of the CIC
+neighbourhood in shared memory or direct loads), keeps the fastest on the octree
+(mt_set_launch_config, mt_set_trace_options) and caches the choice in a JSON file keyed by the
+device name and a workload signature.  Results do not depend on these choices, only the time does.
 
 `TraceGraph` captures one mt_trace_rays call (the queue reset and the persistent launch) in
 a CUDA graph; `replay()` re-runs it on the same buffers (e.g. after the field or the ray
@@ -19,7 +20,16 @@ import torch
 
 from . import binding as B
 
-CANDIDATES = [(128, 4), (128, 3), (64, 8), (64, 6), (256, 2), (256, 1)]
+# (threads per block, blocks per SM, ray chunk, staging: 1 shared-memory neighbourhood, 2 direct loads)
+CANDIDATES = [(128, 4, 32, 1), (128, 3, 32, 1), (64, 8, 32, 1), (256, 2, 32, 1), (256, 1, 32, 1),
+              (128, 4, 64, 1), (128, 4, 128, 1), (128, 4, 32, 2), (64, 8, 32, 2), (256, 2, 32, 2)]
+
+
+def _apply(tree, cand):
+    bs, bps = cand[0], cand[1]
+    chunk, staging = (cand[2], cand[3]) if len(cand) > 2 else (0, 0)
+    tree.set_launch_config(bs, bps)
+    tree.set_trace_options(chunk, staging)
 
 
 def _signature(tree: B.Octree, params: B.TraceParams, n_rays: int) -> str:
@@ -29,7 +39,8 @@ def _signature(tree: B.Octree, params: B.TraceParams, n_rays: int) -> str:
 
 def autotune(tree: B.Octree, params: B.TraceParams, dirs: torch.Tensor, sample: int = 131072, repeats: int = 2,
              cache_path: str | None = None, candidates=CANDIDATES, seed: int = 0):
-    """Pick the fastest launch shape on a sample of the rays; returns {"best": (block, bps), "ms": {...}}."""
+    """Pick the fastest configuration on a sample of the rays; returns {"best": (block, bps, chunk, staging),
+    "ms": {...}}."""
     n = int(dirs.shape[1])
     key = _signature(tree, params, n)
     cache = {}
@@ -37,8 +48,7 @@ def autotune(tree: B.Octree, params: B.TraceParams, dirs: torch.Tensor, sample: 
         with open(cache_path) as f:
             cache = json.load(f)
         if key in cache:
-            best = tuple(cache[key]["best"])
-            tree.set_launch_config(*best)
+            _apply(tree, tuple(cache[key]["best"]))
             return cache[key]
     # sample: a seeded subset of rays, with the cone table cut accordingly
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -52,8 +62,8 @@ def autotune(tree: B.Octree, params: B.TraceParams, dirs: torch.Tensor, sample: 
     sd = dirs[:, torch.from_numpy(idx).to(dirs.device)].contiguous()
     out = B.alloc_outputs(m, dirs.device, names=["n_steps"])
     times = {}
-    for bs, bps in candidates:
-        tree.set_launch_config(bs, bps)
+    for cand in candidates:
+        _apply(tree, cand)
         B.trace_rays(tree, sp, sd, out)
         ts = []
         for _ in range(repeats):
@@ -63,10 +73,10 @@ def autotune(tree: B.Octree, params: B.TraceParams, dirs: torch.Tensor, sample: 
             b.record()
             torch.cuda.synchronize()
             ts.append(a.elapsed_time(b))
-        times[f"{bs}x{bps}"] = float(np.median(ts))
+        times["x".join(str(v) for v in cand)] = float(np.median(ts))
     best_key = min(times, key=times.get)
     best = tuple(int(v) for v in best_key.split("x"))
-    tree.set_launch_config(*best)
+    _apply(tree, best)
     res = {"best": list(best), "ms": times, "sample_rays": m}
     if cache_path:
         cache[key] = res

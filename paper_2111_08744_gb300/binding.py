@@ -97,11 +97,15 @@ def load():
         lib.mt_healpix_bin.argtypes = [P, ctypes.c_int64, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, P, P, P, P]
         lib.mt_deflection.restype = ctypes.c_int
         lib.mt_deflection.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64, P, P, P]
+        lib.mt_field_from_coarse_phi.restype = ctypes.c_int
+        lib.mt_field_from_coarse_phi.argtypes = [P, P, P, ctypes.POINTER(P), ctypes.POINTER(P), P]
         lib.mt_pullback_coarse_phi.restype = ctypes.c_int
         lib.mt_pullback_coarse_phi.argtypes = [P, ctypes.POINTER(P), P, P, P]
         lib.mt_trace_rays_noalloc.restype = ctypes.c_int
         lib.mt_trace_rays_noalloc.argtypes = [P, ctypes.POINTER(mt_trace_params), P, ctypes.c_int64,
                                               ctypes.POINTER(mt_ray_out), P]
+        lib.mt_set_trace_options.restype = ctypes.c_int
+        lib.mt_set_trace_options.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
         lib.mt_set_launch_config.restype = ctypes.c_int
         lib.mt_set_launch_config.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
         lib.mt_device_status.restype = ctypes.c_int
@@ -241,6 +245,9 @@ class Octree:
         nbytes = ctypes.c_int64()
         _check(load().mt_octree_info(self.handle, cells, ctypes.byref(nbytes)), "mt_octree_info")
         return list(cells), int(nbytes.value)
+
+    def set_trace_options(self, ray_chunk=0, staging=0):
+        _check(load().mt_set_trace_options(self.handle, int(ray_chunk), int(staging)), "mt_set_trace_options")
 
     def set_launch_config(self, block_size=0, blocks_per_sm=0):
         _check(load().mt_set_launch_config(self.handle, int(block_size), int(blocks_per_sm)), "mt_set_launch_config")
@@ -516,3 +523,27 @@ def probe_fp64_fma_rate(iters: int = 1 << 14, repeats: int = 3, stream=None) -> 
     _check(mt_probe_fp64_fma_rate(int(iters), int(repeats), ctypes.byref(v), _stream_handle(stream)),
            "mt_probe_fp64_fma_rate")
     return float(v.value)
+
+
+def mt_field_from_coarse_phi(tree, phi0, slice_weight, base, records, stream):
+    return load().mt_field_from_coarse_phi(tree, phi0, slice_weight, base, records, stream)
+
+
+def field_from_coarse_phi(tree: Octree, phi0_morton, slice_weight, base=None, stream=None):
+    """mt_field_from_coarse_phi on CUDA tensors: the records of every level (float64 tensors
+    [count, n_slices, 4]) from the coarse potential phi0 ([N^3] float64, Morton order); base: the
+    phi0-independent records per level (same shapes) or None."""
+    torch = _require_cuda()
+    cells, _ = tree.info()
+    dev = phi0_morton.device
+    recs = [torch.empty((c, tree.n_slices, 4), dtype=torch.float64, device=dev) for c in cells]
+    out = (ctypes.c_void_p * len(recs))(*[t.data_ptr() if t.numel() else None for t in recs])
+    bp = None
+    if base is not None:
+        keep = [b.contiguous() for b in base]
+        bp = (ctypes.c_void_p * len(keep))(*[b.data_ptr() if b.numel() else None for b in keep])
+    sw = np.ascontiguousarray(slice_weight, dtype=np.float64)
+    phi = phi0_morton.contiguous()
+    _check(mt_field_from_coarse_phi(tree.handle, phi.data_ptr(), sw.ctypes.data_as(ctypes.c_void_p), bp, out,
+                                    _stream_handle(stream)), "mt_field_from_coarse_phi")
+    return recs

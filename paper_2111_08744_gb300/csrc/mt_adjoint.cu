@@ -9,8 +9,9 @@
 //      `checkpoint_every` steps in a global checkpoint buffer;
 //   2. from the cotangent dL/dxi of the end point on the iso-eta surface,
 //      xi = x - (k/k0)(eta - eta_stop), form the cotangent of the final state;
-//   3. for each segment, last to first: recompute its steps from the checkpoint into a
-//      per-thread buffer, then run each step backward: recompute the 4 RK4 stages, and apply
+//   3. for each segment, last to first (a warp's 32 rays in lockstep, aligned on their last
+//      segments): recompute its steps from the checkpoint into a per-thread buffer, then run each
+//      step backward: recompute the 4 RK4 stages, and apply
 //      the transposed stage Jacobians (including the dependence of the step size on the state
 //      and of the shortened last step), scattering the cotangents of grad phi and phi_eta at
 //      every stage onto the 8 CIC records of both bracketing slices with FP64 atomics;
@@ -206,6 +207,74 @@ __device__ bool step_size(const DevField& F, const TraceArgs& A, const double* y
   return true;
 }
 
+// Reverse of one FP64 step from the step-start state y (x[3], eta, k0, k[3]): yb holds the cotangent
+// of the step's end state on entry and of its start state on return; last: the ray's final
+// (shortened) step.  False if a stage left a non-periodic domain.
+template <class T>
+__device__ bool reverse_step_fp64(const DevField& F, const TraceArgs& A, bool grav, const double* y, bool last,
+                                  double eta_stop, double* yb, const RecBar& R, unsigned* err, const ScatterCache* sc) {
+  double y10[10];
+  for (int i = 0; i < 8; ++i) y10[i] = y[i];
+  y10[8] = y10[9] = 0.0;
+  double K1[10], K2[10], K3[10], K4[10], Y2[10], Y3[10], Y4[10], h;
+  if (!step_size<T>(F, A, y10, eta_stop, last, K1, &h, err)) return false;
+  const double h2 = 0.5 * h;
+  for (int i = 0; i < 10; ++i) Y2[i] = y10[i] + h2 * K1[i];
+  geodesic_rhs<T>(F, grav, Y2, K2, nullptr, err);
+  for (int i = 0; i < 10; ++i) Y3[i] = y10[i] + h2 * K2[i];
+  geodesic_rhs<T>(F, grav, Y3, K3, nullptr, err);
+  for (int i = 0; i < 10; ++i) Y4[i] = y10[i] + h * K3[i];
+  geodesic_rhs<T>(F, grav, Y4, K4, nullptr, err);
+  // reverse of y' = y + h/6 (K1 + 2 K2 + 2 K3 + K4)
+  double hbar = 0.0, kb1[8], kb2[8], kb3[8], kb4[8], nyb[8];
+  for (int i = 0; i < 8; ++i) {
+    hbar += yb[i] * (K1[i] + 2.0 * K2[i] + 2.0 * K3[i] + K4[i]) / 6.0;
+    kb1[i] = yb[i] * (h / 6.0);
+    kb2[i] = yb[i] * (h / 3.0);
+    kb3[i] = yb[i] * (h / 3.0);
+    kb4[i] = yb[i] * (h / 6.0);
+    nyb[i] = yb[i];
+  }
+  double Yb[8];
+  // stage 4 at Y4 = y + h K3
+  for (int i = 0; i < 8; ++i) Yb[i] = 0.0;
+  stage_adjoint<T>(F, grav, Y4, kb4, Yb, R, err, sc);
+  for (int i = 0; i < 8; ++i) {
+    nyb[i] += Yb[i];
+    kb3[i] += h * Yb[i];
+    hbar += Yb[i] * K3[i];
+  }
+  // stage 3 at Y3 = y + h/2 K2
+  for (int i = 0; i < 8; ++i) Yb[i] = 0.0;
+  stage_adjoint<T>(F, grav, Y3, kb3, Yb, R, err, sc);
+  for (int i = 0; i < 8; ++i) {
+    nyb[i] += Yb[i];
+    kb2[i] += h2 * Yb[i];
+    hbar += 0.5 * Yb[i] * K2[i];
+  }
+  // stage 2 at Y2 = y + h/2 K1
+  for (int i = 0; i < 8; ++i) Yb[i] = 0.0;
+  stage_adjoint<T>(F, grav, Y2, kb2, Yb, R, err, sc);
+  for (int i = 0; i < 8; ++i) {
+    nyb[i] += Yb[i];
+    kb1[i] += h2 * Yb[i];
+    hbar += 0.5 * Yb[i] * K1[i];
+  }
+  // stage 1 at y
+  for (int i = 0; i < 8; ++i) Yb[i] = 0.0;
+  stage_adjoint<T>(F, grav, y10, kb1, Yb, R, err, sc);
+  for (int i = 0; i < 8; ++i) nyb[i] += Yb[i];
+  // step size: h = dx_l / (N |k0|), or (eta_stop - eta) / k0 on the last step
+  const double k0 = y[4];
+  if (last) nyb[3] += -hbar / k0;
+  nyb[4] += -hbar * h / k0;
+  for (int i = 0; i < 8; ++i) yb[i] = nyb[i];
+  return true;
+}
+
+// Warp-synchronous sweep (as the mixed-precision one): a warp takes 32 consecutive rays per turn,
+// integrates them forward together, then reverses them segment by segment aligned on each ray's last
+// segment, with warp-uniform loop bounds.
 template <class T>
 __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(DevField F, DevCones C, const double* __restrict__ dirs,
                                                             OutPtrs O, TraceArgs A, const double* __restrict__ dL_dxi,
@@ -224,150 +293,99 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_kernel(DevField F, DevCones
   sc.key = (int4*)((unsigned*)(adj_smem + 64 * kAdjBlock) + 8 * kAdjBlock) + threadIdx.x;
   for (int j = 0; j < 64; ++j) sc.acc[j * sc.stride] = 0.0;
   *sc.key = make_int4(-1, 0, 0, 0);
-  long long ray = -1;
-  bool exhausted = false;
   for (;;) {
-    // one ray per lane per turn of the loop (rays take very different times; refill as in the traces)
-    const bool need = (ray < 0) && !exhausted;
-    const unsigned m = __ballot_sync(0xffffffffu, need);
-    if (m) {
-      const int leader = __ffs(m) - 1;
-      unsigned long long base = 0;
-      if ((int)lane == leader) base = atomicAdd(ws, (unsigned long long)__popc(m));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (need) {
-        const long long id = (long long)base + __popc(m & ((1u << lane) - 1u));
-        if (id < n) ray = id; else exhausted = true;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(ws, 32ull);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= (unsigned long long)n) break;
+    const long long ray = (long long)base + lane;
+    const bool have = ray < n;
+    RayState r;
+    long long off = 0, n_ck = 0;
+    bool ok = have;
+    double k_init_scale = 0.0;
+    if (have) {
+      int c = 0;
+      while (c + 1 < C.n && C.begin[c + 1] <= ray) ++c;
+      r = ray_start<T>(F, C.obs[c], C.eta_stop[c], dirs, n, ray, grav, err);
+      k_init_scale = sqrt(r.y[5] * r.y[5] + r.y[6] * r.y[6] + r.y[7] * r.y[7]);
+      off = ck_off[ray];
+      n_ck = ck_off[ray + 1] - off;
+    }
+    // 1. forward with checkpoints, the warp's rays in lockstep
+    bool fwd = have;
+    while (__any_sync(0xffffffffu, fwd)) {
+      if (fwd) {
+        if (r.n_steps % seg_len == 0) {
+          const long long j = r.n_steps / seg_len;
+          if (j >= n_ck) {
+            atomicOr(err, kErrOOB);  // more steps than the first pass counted
+            ok = false;
+            fwd = false;
+          } else {
+            double* cp = ckpt + (off + j) * 8;
+            for (int i = 0; i < 8; ++i) cp[i] = r.y[i];
+          }
+        }
+        if (fwd && ray_step_fp64<T>(F, A, r, err)) fwd = false;
       }
     }
-    if (!__any_sync(0xffffffffu, ray >= 0)) break;
-    if (ray < 0) continue;
-    int c = 0;
-    while (c + 1 < C.n && C.begin[c + 1] <= ray) ++c;
-    RayState r = ray_start<T>(F, C.obs[c], C.eta_stop[c], dirs, n, ray, grav, err);
-    const double k_init_scale = sqrt(r.y[5] * r.y[5] + r.y[6] * r.y[6] + r.y[7] * r.y[7]);
-    // 1. forward with checkpoints
-    const long long off = ck_off[ray], n_ck = ck_off[ray + 1] - ck_off[ray];
-    bool ok = true;
-    for (;;) {
-      if (r.n_steps % seg_len == 0) {
-        const long long j = r.n_steps / seg_len;
-        if (j >= n_ck) {
-          atomicOr(err, kErrOOB);  // more steps than the first pass counted
-          ok = false;
-          break;
-        }
-        double* cp = ckpt + (off + j) * 8;
-        for (int i = 0; i < 8; ++i) cp[i] = r.y[i];
+    if (have) ray_finish<T>(F, A, r, ray, n, O, err);
+    const bool active = ok && have && r.status == MT_RAY_OK && r.n_steps > 0;
+    const int n_steps = active ? r.n_steps : 0;
+    const int n_seg = (n_steps + seg_len - 1) / seg_len;
+    const int max_seg = (int)__reduce_max_sync(0xffffffffu, (unsigned)n_seg);
+    // 2. cotangent of the end state from dL/dxi
+    double yb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (active) {
+      const double* y = r.y;
+      const double k0 = y[4], de = y[3] - r.eta_stop;
+      const double xb[3] = {dL_dxi[ray], dL_dxi[n + ray], dL_dxi[2 * n + ray]};
+      const double xk = xb[0] * y[5] + xb[1] * y[6] + xb[2] * y[7];
+      for (int d = 0; d < 3; ++d) {
+        yb[d] = xb[d];
+        yb[5 + d] = -xb[d] * de / k0;
       }
-      if (ray_step_fp64<T>(F, A, r, err)) break;
+      yb[3] = -xk / k0;
+      yb[4] = xk * de / (k0 * k0);
     }
-    ray_finish<T>(F, A, r, ray, n, O, err);
-    const int n_steps = r.n_steps;
-    if (ok && r.status == MT_RAY_OK && n_steps > 0) {
-      // 2. cotangent of the end state from dL/dxi
-      double yb[8];
-      {
-        const double* y = r.y;
-        const double k0 = y[4], de = y[3] - r.eta_stop;
-        const double xb[3] = {dL_dxi[ray], dL_dxi[n + ray], dL_dxi[2 * n + ray]};
-        const double xk = xb[0] * y[5] + xb[1] * y[6] + xb[2] * y[7];
-        for (int d = 0; d < 3; ++d) {
-          yb[d] = xb[d];
-          yb[5 + d] = -xb[d] * de / k0;
-        }
-        yb[3] = -xk / k0;
-        yb[4] = xk * de / (k0 * k0);
-      }
-      // 3. segments, last to first
-      const int n_seg = (n_steps + seg_len - 1) / seg_len;
-      for (int sgi = n_seg - 1; sgi >= 0 && ok; --sgi) {
-        const int s0 = sgi * seg_len;
-        const int s1 = min(n_steps, s0 + seg_len);
-        RayState q = r;
+    // 3. segments from the last, aligned on each ray's last segment
+    bool alive = active;
+    for (int j = max_seg - 1; j >= 0; --j) {
+      const int sgi = j - (max_seg - n_seg);
+      const bool on = alive && sgi >= 0;
+      const int s0 = on ? sgi * seg_len : 0;
+      const int len = on ? min(n_steps, s0 + seg_len) - s0 : 0;
+      RayState q = r;
+      if (on) {
         const double* cp = ckpt + (off + sgi) * 8;
         for (int i = 0; i < 8; ++i) q.y[i] = cp[i];
         q.n_steps = s0;
-        for (int st = s0; st < s1; ++st) {
-          for (int i = 0; i < 8; ++i) ys[st - s0][i] = q.y[i];
-          if (st + 1 < s1) ray_step_fp64<T>(F, A, q, err);
-        }
-        for (int st = s1 - 1; st >= s0; --st) {
-          const double* y = ys[st - s0];
-          double y10[10];
-          for (int i = 0; i < 8; ++i) y10[i] = y[i];
-          y10[8] = y10[9] = 0.0;
-          double K1[10], K2[10], K3[10], K4[10], Y2[10], Y3[10], Y4[10], h;
-          if (!step_size<T>(F, A, y10, r.eta_stop, st == n_steps - 1, K1, &h, err)) {
-            ok = false;
-            break;
-          }
-          const double h2 = 0.5 * h;
-          for (int i = 0; i < 10; ++i) Y2[i] = y10[i] + h2 * K1[i];
-          geodesic_rhs<T>(F, grav, Y2, K2, nullptr, err);
-          for (int i = 0; i < 10; ++i) Y3[i] = y10[i] + h2 * K2[i];
-          geodesic_rhs<T>(F, grav, Y3, K3, nullptr, err);
-          for (int i = 0; i < 10; ++i) Y4[i] = y10[i] + h * K3[i];
-          geodesic_rhs<T>(F, grav, Y4, K4, nullptr, err);
-          // reverse of y' = y + h/6 (K1 + 2 K2 + 2 K3 + K4)
-          double hbar = 0.0, kb1[8], kb2[8], kb3[8], kb4[8], nyb[8];
-          for (int i = 0; i < 8; ++i) {
-            hbar += yb[i] * (K1[i] + 2.0 * K2[i] + 2.0 * K3[i] + K4[i]) / 6.0;
-            kb1[i] = yb[i] * (h / 6.0);
-            kb2[i] = yb[i] * (h / 3.0);
-            kb3[i] = yb[i] * (h / 3.0);
-            kb4[i] = yb[i] * (h / 6.0);
-            nyb[i] = yb[i];
-          }
-          double Yb[8];
-          // stage 4 at Y4 = y + h K3
-          for (int i = 0; i < 8; ++i) Yb[i] = 0.0;
-          stage_adjoint<T>(F, grav, Y4, kb4, Yb, R, err, &sc);
-          for (int i = 0; i < 8; ++i) {
-            nyb[i] += Yb[i];
-            kb3[i] += h * Yb[i];
-            hbar += Yb[i] * K3[i];
-          }
-          // stage 3 at Y3 = y + h/2 K2
-          for (int i = 0; i < 8; ++i) Yb[i] = 0.0;
-          stage_adjoint<T>(F, grav, Y3, kb3, Yb, R, err, &sc);
-          for (int i = 0; i < 8; ++i) {
-            nyb[i] += Yb[i];
-            kb2[i] += h2 * Yb[i];
-            hbar += 0.5 * Yb[i] * K2[i];
-          }
-          // stage 2 at Y2 = y + h/2 K1
-          for (int i = 0; i < 8; ++i) Yb[i] = 0.0;
-          stage_adjoint<T>(F, grav, Y2, kb2, Yb, R, err, &sc);
-          for (int i = 0; i < 8; ++i) {
-            nyb[i] += Yb[i];
-            kb1[i] += h2 * Yb[i];
-            hbar += 0.5 * Yb[i] * K1[i];
-          }
-          // stage 1 at y
-          for (int i = 0; i < 8; ++i) Yb[i] = 0.0;
-          stage_adjoint<T>(F, grav, y10, kb1, Yb, R, err, &sc);
-          for (int i = 0; i < 8; ++i) nyb[i] += Yb[i];
-          // step size: h = dx_l / (N |k0|), or (eta_stop - eta) / k0 on the last step
-          const double k0 = y[4];
-          if (st == n_steps - 1) nyb[3] += -hbar / k0;
-          nyb[4] += -hbar * h / k0;
-          for (int i = 0; i < 8; ++i) yb[i] = nyb[i];
+      }
+      for (int st = 0; st < seg_len; ++st) {
+        if (st < len) {
+          for (int i = 0; i < 8; ++i) ys[st][i] = q.y[i];
+          if (st + 1 < len) ray_step_fp64<T>(F, A, q, err);
         }
       }
-      // 4. initial wave vector k = n sqrt((1 + 2 phi_o)/(1 - 2 phi_o)) depends on phi_o
-      if (ok && grav) {
-        const double nd[3] = {__ldg(&dirs[ray]), __ldg(&dirs[n + ray]), __ldg(&dirs[2 * n + ray])};
-        const double po = r.phi_o;
-        const double dkn = 2.0 / (k_init_scale / sqrt(nd[0] * nd[0] + nd[1] * nd[1] + nd[2] * nd[2]) *
-                                  (1.0 - 2.0 * po) * (1.0 - 2.0 * po));
-        const double phib = (yb[5] * nd[0] + yb[6] * nd[1] + yb[7] * nd[2]) * dkn;
-        const double zero[3] = {0.0, 0.0, 0.0};
-        scatter_cotangent<T>(F, r.xo, F.eta_o, zero, 0.0, phib, R, err, &sc);
+      for (int st = seg_len - 1; st >= 0; --st) {
+        if (st < len && alive) {
+          if (!reverse_step_fp64<T>(F, A, grav, ys[st], s0 + st == n_steps - 1, r.eta_stop, yb, R, err, &sc))
+            alive = false;
+        }
       }
     }
+    // 4. initial wave vector k = n sqrt((1 + 2 phi_o)/(1 - 2 phi_o)) depends on phi_o
+    if (alive && grav) {
+      const double nd[3] = {__ldg(&dirs[ray]), __ldg(&dirs[n + ray]), __ldg(&dirs[2 * n + ray])};
+      const double po = r.phi_o;
+      const double dkn = 2.0 / (k_init_scale / sqrt(nd[0] * nd[0] + nd[1] * nd[1] + nd[2] * nd[2]) *
+                                (1.0 - 2.0 * po) * (1.0 - 2.0 * po));
+      const double phib = (yb[5] * nd[0] + yb[6] * nd[1] + yb[7] * nd[2]) * dkn;
+      const double zero[3] = {0.0, 0.0, 0.0};
+      scatter_cotangent<T>(F, r.xo, F.eta_o, zero, 0.0, phib, R, err, &sc);
+    }
     scatter_flush(F, R, sc);
-    ray = -1;
   }
 }
 
@@ -484,7 +502,7 @@ extern "C" mt_status mt_trace_rays_adjoint(const mt_octree* tree, const mt_trace
   TraceArgs A;
   A.steps_per_cell = params->steps_per_cell;
   A.interp = params->interp;
-  A.pad = 0;
+  A.ray_chunk = 32;
   A.gravity_on = params->gravity_on ? 1 : 0;
   A.max_steps = params->max_steps;
   A.n_rays = n_rays;

@@ -3,7 +3,7 @@
 // loss on the end points with respect to the records (Sect. 2.2: RK4 of Eqs. 2-4, CIC with level
 // fallback, slices linear in eta).
 //
-// Per ray (one lane of a persistent warp, rays claimed in chunks of consecutive ids):
+// Per ray (one lane; a warp takes 32 consecutive ray ids at a time and runs their phases in lockstep):
 //   1. integrate forward with the mixed step, keeping the FP64 state every `checkpoint_every` steps;
 //   2. form the cotangent of the final state from dL/dxi, xi = x - (k/k0)(eta - eta_stop);
 //   3. for each segment, last to first: recompute its states from the checkpoint, then reverse each
@@ -176,7 +176,8 @@ __device__ bool reverse_step_mixed(const DevField& F, const TraceArgs& A, const 
   bool last = false;
   {
     float offx[3] = {0.0f, 0.0f, 0.0f}, offe = 0.0f, offk0 = 0.0f, offk[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
+    // one copy of the stage code (an unrolled kernel outgrows the instruction cache)
+#pragma unroll 1
     for (int st = 0; st < 4; ++st) {
       const float k0v = k0s + offk0;
       const float kv[3] = {ks[0] + offk[0], ks[1] + offk[1], ks[2] + offk[2]};
@@ -220,20 +221,20 @@ __device__ bool reverse_step_mixed(const DevField& F, const TraceArgs& A, const 
   const double hd = (double)h;
   double hbar = yb[0] * y[5] + yb[1] * y[6] + yb[2] * y[7] + yb[3] * y[4];
   float hbar_f = 0.0f;
-  float Kb[4][8];
+  float ybf[8];
 #pragma unroll
+  for (int i = 0; i < 8; ++i) ybf[i] = (float)yb[i];
+#pragma unroll 1
   for (int st = 0; st < 4; ++st) {
     const float b = (st == 0 || st == 3) ? (1.0f / 6.0f) : (1.0f / 3.0f);
-    const float bh = b * h;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) Kb[st][i] = bh * (float)yb[i];
-    hbar_f += b * ((float)yb[0] * okk[st][1] + (float)yb[1] * okk[st][2] + (float)yb[2] * okk[st][3] +
-                   (float)yb[3] * okk[st][0] + (float)yb[4] * Kk[st][0] + (float)yb[5] * Kk[st][1] +
-                   (float)yb[6] * Kk[st][2] + (float)yb[7] * Kk[st][3]);
+    hbar_f += b * (ybf[0] * okk[st][1] + ybf[1] * okk[st][2] + ybf[2] * okk[st][3] + ybf[3] * okk[st][0] +
+                   ybf[4] * Kk[st][0] + ybf[5] * Kk[st][1] + ybf[6] * Kk[st][2] + ybf[7] * Kk[st][3]);
   }
-  // stages from the last to the first: Y_j = y + a_{j-1} h K_{j-1}
+  // stages from the last to the first.  Stage j sits at y + a_{j-1} h K_{j-1}, so the cotangent of
+  // K_j is b_j h yb' (the step's sum) plus a_j h times the cotangent of stage j + 1's state.
   float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // sum of the stage-state cotangents (added to yb in FP64)
-#pragma unroll
+  float tbn[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // cotangent of the state of the stage after this one
+#pragma unroll 1
   for (int st = 3; st >= 0; --st) {
     float offx[3] = {0.0f, 0.0f, 0.0f}, offe = 0.0f;
     const float a = st == 3 ? 1.0f : 0.5f;  // stage st sits at y + a h K_{st-1}
@@ -249,6 +250,11 @@ __device__ bool reverse_step_mixed(const DevField& F, const TraceArgs& A, const 
       offx[2] = c * kp[2];
       offe = c * kp0;
     }
+    const float b = (st == 0 || st == 3) ? (1.0f / 6.0f) : (1.0f / 3.0f);
+    const float an = st == 2 ? 1.0f : 0.5f;  // stage st + 1 sits at y + an h K_st
+    float Kb[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) Kb[i] = b * h * ybf[i] + (st < 3 ? an * h * tbn[i] : 0.0f);
     const float k0v = k0s + okk[st][0];
     const float kv[3] = {ks[0] + okk[st][1], ks[1] + okk[st][2], ks[2] + okk[st][3]};
     float Kk0, Kkv[3], KI, Ks;
@@ -256,21 +262,17 @@ __device__ bool reverse_step_mixed(const DevField& F, const TraceArgs& A, const 
     if (!rhs_mixed<true, MT_INTERP_CIC>(F, Grav, B, eta, offx, offe, k0v, kv, &Kk0, Kkv, &KI, &Ks, nullptr, err,
                                         lc, &sf))
       return false;
-    float tb[8], gbar[3], pebar;
-    stage_adjoint_mixed(sf, k0v, kv, Kb[st], tb, gbar, &pebar);
+    float gbar[3], pebar;
+    stage_adjoint_mixed(sf, k0v, kv, Kb, tbn, gbar, &pebar);
     if (Grav) acc_add(F, R, sc, sf, gbar, pebar, err);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i] += tb[i];
+    for (int i = 0; i < 8; ++i) acc[i] += tbn[i];
     if (st > 0) {
-      const float c = a * h;
-      // Y_st = y + c K_{st-1}, K_{st-1} = (k, k0, Kk0, Kk) of stage st - 1
+      // Y_st = y + a h K_{st-1}, K_{st-1} = (k, k0, Kk0, Kk) of stage st - 1
       const float Kprev[8] = {kp[0], kp[1], kp[2], kp0, Kk[st - 1][0], Kk[st - 1][1], Kk[st - 1][2], Kk[st - 1][3]};
       float dot = 0.0f;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        Kb[st - 1][i] += c * tb[i];
-        dot += tb[i] * Kprev[i];
-      }
+      for (int i = 0; i < 8; ++i) dot += tbn[i] * Kprev[i];
       hbar_f += a * dot;
     }
   }
@@ -360,8 +362,52 @@ __global__ void __launch_bounds__(kAdjMBlock) count_mixed_kernel(DevField F, Dev
   }
 }
 
+// Scatter the cotangent phib of phi at the observer (the initial wave vector depends on it) onto the
+// CIC records ray_start sampled there (FP64 coordinates, FP32 weights, the slice bracket of eta_o).
+__device__ void scatter_observer(const DevField& F, const RecBarM& R, const double* xo, double phib, unsigned* err) {
+  double u[3];
+  if (!coarse_coords<float>(F, xo, u)) return;
+  const int lfin = locate_level(F, u, err);
+  int s = 0;
+  while (s < F.S - 2 && F.seta[s + 1] <= F.eta_o) ++s;
+  for (int l = lfin; l >= 0; --l) {
+    const double scl = (double)(1ll << l);
+    long long i0[3];
+    float f[3];
+    for (int d = 0; d < 3; ++d) {
+      const double U = u[d] * scl - 0.5;
+      const double fl = floor(U);
+      i0[d] = (long long)fl;
+      f[d] = (float)(U - fl);
+    }
+    unsigned rows[8];
+    if (!cic_rows(F, l, i0, rows, err)) continue;
+    double* base = R.lv[l];
+    if (!base) return;
+    const float wt = F.S > 1 ? (float)((F.eta_o - F.seta[s]) / (F.seta[s + 1] - F.seta[s])) : 0.0f;
+    for (int c = 0; c < 8; ++c) {
+      const float wx = (c & 1) ? f[0] : 1.0f - f[0];
+      const float wy = (c & 2) ? f[1] : 1.0f - f[1];
+      const float wz = (c & 4) ? f[2] : 1.0f - f[2];
+      const double w = (double)(wx * wy * wz);
+      double* r0 = base + ((size_t)rows[c] * F.S + s) * 4;
+      if (F.S == 1) {
+        atomicAdd(r0, w * phib);
+      } else {
+        atomicAdd(r0, w * (double)(1.0f - wt) * phib);
+        atomicAdd(r0 + 4, w * (double)wt * phib);
+      }
+    }
+    return;
+  }
+}
+
+// Warp-synchronous sweep: a warp takes 32 consecutive rays per turn (sky neighbours), integrates
+// them forward together (lanes whose ray has ended wait), then reverses them segment by segment,
+// aligned on each ray's last segment, with warp-uniform loop bounds, so that the lanes run the same
+// phase (recompute or reverse) at the same time; only the rays' different step counts leave lanes idle.
 template <bool Grav>
-__global__ void __launch_bounds__(kAdjMBlock) adjoint_mixed_kernel(DevField F, DevCones C,
+__global__ void __launch_bounds__(kAdjMBlock, 3) adjoint_mixed_kernel(DevField F, DevCones C,
                                                                    const double* __restrict__ dirs, OutPtrs O,
                                                                    TraceArgs A, const double* __restrict__ dL_dxi,
                                                                    RecBarM R, double* ckpt, const long long* ck_off,
@@ -381,124 +427,100 @@ __global__ void __launch_bounds__(kAdjMBlock) adjoint_mixed_kernel(DevField F, D
   double ys[kMaxSegmentM][8];
   const unsigned lane = threadIdx.x & 31u;
   const long long n = A.n_rays;
-  WarpQueue q;
-  long long ray = -1;
-  bool exhausted = false;
   for (;;) {
-    const bool need = ray < 0 && !exhausted;
-    const long long id = q.next(need, lane, ws);
-    if (need) {
-      if (id >= 0 && id < n) ray = id;
-      else exhausted = true;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(ws, (unsigned long long)kAdjMChunk);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= (unsigned long long)n) break;
+    const long long ray = (long long)base + lane;
+    const bool have = ray < n;
+    RayState r;
+    long long off = 0, n_ck = 0;
+    bool ok = have;
+    if (have) {
+      int c = 0;
+      while (c + 1 < C.n && C.begin[c + 1] <= ray) ++c;
+      r = ray_start<float>(F, C.obs[c], C.eta_stop[c], dirs, n, ray, Grav, err);
+      off = ck_off[ray];
+      n_ck = ck_off[ray + 1] - off;
     }
-    if (!__any_sync(0xffffffffu, ray >= 0)) break;
-    if (ray < 0) continue;
-    int c = 0;
-    while (c + 1 < C.n && C.begin[c + 1] <= ray) ++c;
-    RayState r = ray_start<float>(F, C.obs[c], C.eta_stop[c], dirs, n, ray, Grav, err);
     *lc.key = make_int4(-1, 0, 0, 0);
-    // 1. forward with checkpoints
-    const long long off = ck_off[ray], n_ck = ck_off[ray + 1] - ck_off[ray];
-    bool ok = true;
-    for (;;) {
-      if (r.n_steps % seg_len == 0) {
-        const long long j = r.n_steps / seg_len;
-        if (j >= n_ck) {
-          atomicOr(err, kErrOOB);  // more steps than the counting pass found
-          ok = false;
-          break;
-        }
-        double* cp = ckpt + (off + j) * 8;
-        for (int i = 0; i < 8; ++i) cp[i] = r.y[i];
-      }
-      if (ray_step_mixed<MT_INTERP_CIC>(F, A, r, err, &lc)) break;
-    }
-    ray_finish<float>(F, A, r, ray, n, O, err);
-    const int n_steps = r.n_steps;
-    if (ok && r.status == MT_RAY_OK && n_steps > 0) {
-      // 2. cotangent of the end state from dL/dxi
-      double yb[8];
-      {
-        const double* y = r.y;
-        const double k0 = y[4], de = y[3] - r.eta_stop;
-        const double xb[3] = {dL_dxi[ray], dL_dxi[n + ray], dL_dxi[2 * n + ray]};
-        const double xk = xb[0] * y[5] + xb[1] * y[6] + xb[2] * y[7];
-        for (int d = 0; d < 3; ++d) {
-          yb[d] = xb[d];
-          yb[5 + d] = -xb[d] * de / k0;
-        }
-        yb[3] = -xk / k0;
-        yb[4] = xk * de / (k0 * k0);
-      }
-      // 3. segments, last to first
-      const int n_seg = (n_steps + seg_len - 1) / seg_len;
-      for (int sgi = n_seg - 1; sgi >= 0 && ok; --sgi) {
-        const int s0 = sgi * seg_len;
-        const int s1 = min(n_steps, s0 + seg_len);
-        RayState qs = r;
-        const double* cp = ckpt + (off + sgi) * 8;
-        for (int i = 0; i < 8; ++i) qs.y[i] = cp[i];
-        qs.n_steps = s0;
-        for (int st = s0; st < s1; ++st) {
-          for (int i = 0; i < 8; ++i) ys[st - s0][i] = qs.y[i];
-          if (st + 1 < s1) ray_step_mixed<MT_INTERP_CIC>(F, A, qs, err, &lc);
-        }
-        for (int st = s1 - 1; st >= s0; --st) {
-          if (!reverse_step_mixed<Grav>(F, A, ys[st - s0], r.eta_stop, yb, &lc, sc, R, err)) {
+    // 1. forward with checkpoints, the warp's rays in lockstep
+    bool fwd = have;
+    while (__any_sync(0xffffffffu, fwd)) {
+      if (fwd) {
+        if (r.n_steps % seg_len == 0) {
+          const long long j = r.n_steps / seg_len;
+          if (j >= n_ck) {
+            atomicOr(err, kErrOOB);  // more steps than the counting pass found
             ok = false;
-            break;
+            fwd = false;
+          } else {
+            double* cp = ckpt + (off + j) * 8;
+            for (int i = 0; i < 8; ++i) cp[i] = r.y[i];
           }
         }
+        if (fwd && ray_step_mixed<MT_INTERP_CIC>(F, A, r, err, &lc)) fwd = false;
       }
-      // 4. the initial wave vector k = n sqrt((1 + 2 phi_o)/(1 - 2 phi_o)) depends on phi_o (CIC at
-      //    the observer, as ray_start samples it)
-      if (ok && Grav) {
-        const double nd[3] = {__ldg(&dirs[ray]), __ldg(&dirs[n + ray]), __ldg(&dirs[2 * n + ray])};
-        const double po = r.phi_o;
-        const double kn = sqrt((1.0 + 2.0 * po) / (1.0 - 2.0 * po));
-        const double phib = (yb[5] * nd[0] + yb[6] * nd[1] + yb[7] * nd[2]) * 2.0 / (kn * (1.0 - 2.0 * po) *
-                                                                                     (1.0 - 2.0 * po));
-        double u[3];
-        if (coarse_coords<float>(F, r.xo, u)) {
-          const int lfin = locate_level(F, u, err);
-          int s = 0;
-          while (s < F.S - 2 && F.seta[s + 1] <= F.eta_o) ++s;
-          for (int l = lfin; l >= 0; --l) {
-            const double scl = (double)(1ll << l);
-            long long i0[3];
-            float f[3];
-            for (int d = 0; d < 3; ++d) {
-              const double U = u[d] * scl - 0.5;
-              const double fl = floor(U);
-              i0[d] = (long long)fl;
-              f[d] = (float)(U - fl);
-            }
-            unsigned rows[8];
-            if (!cic_rows(F, l, i0, rows, err)) continue;
-            double* base = R.lv[l];
-            if (base) {
-              const float wt = F.S > 1 ? (float)((F.eta_o - F.seta[s]) / (F.seta[s + 1] - F.seta[s])) : 0.0f;
-              for (int cc = 0; cc < 8; ++cc) {
-                const float wx = (cc & 1) ? f[0] : 1.0f - f[0];
-                const float wy = (cc & 2) ? f[1] : 1.0f - f[1];
-                const float wz = (cc & 4) ? f[2] : 1.0f - f[2];
-                const double w = (double)(wx * wy * wz);
-                double* r0 = base + ((size_t)rows[cc] * F.S + s) * 4;
-                if (F.S == 1) {
-                  atomicAdd(r0, w * phib);
-                } else {
-                  atomicAdd(r0, w * (double)(1.0f - wt) * phib);
-                  atomicAdd(r0 + 4, w * (double)wt * phib);
-                }
-              }
-            }
-            break;
-          }
+    }
+    if (have) ray_finish<float>(F, A, r, ray, n, O, err);
+    const bool active = ok && have && r.status == MT_RAY_OK && r.n_steps > 0;
+    const int n_steps = active ? r.n_steps : 0;
+    const int n_seg = (n_steps + seg_len - 1) / seg_len;
+    const int max_seg = (int)__reduce_max_sync(0xffffffffu, (unsigned)n_seg);
+    // 2. cotangent of the end state from dL/dxi
+    double yb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (active) {
+      const double* y = r.y;
+      const double k0 = y[4], de = y[3] - r.eta_stop;
+      const double xb[3] = {dL_dxi[ray], dL_dxi[n + ray], dL_dxi[2 * n + ray]};
+      const double xk = xb[0] * y[5] + xb[1] * y[6] + xb[2] * y[7];
+      for (int d = 0; d < 3; ++d) {
+        yb[d] = xb[d];
+        yb[5 + d] = -xb[d] * de / k0;
+      }
+      yb[3] = -xk / k0;
+      yb[4] = xk * de / (k0 * k0);
+    }
+    // 3. segments from the last, aligned on each ray's last segment
+    bool alive = active;
+    for (int j = max_seg - 1; j >= 0; --j) {
+      const int sgi = j - (max_seg - n_seg);
+      const bool on = alive && sgi >= 0;
+      const int s0 = on ? sgi * seg_len : 0;
+      const int len = on ? min(n_steps, s0 + seg_len) - s0 : 0;
+      RayState q = r;
+      if (on) {
+        const double* cp = ckpt + (off + sgi) * 8;
+        for (int i = 0; i < 8; ++i) q.y[i] = cp[i];
+        q.n_steps = s0;
+      }
+      // every lane runs these loops with the same bounds, so all 32 reach each __syncwarp: the warp
+      // reconverges after every step instead of letting its lanes drift apart in the branches
+      for (int st = 0; st < seg_len; ++st) {
+        if (st < len) {
+          for (int i = 0; i < 8; ++i) ys[st][i] = q.y[i];
+          if (st + 1 < len) ray_step_mixed<MT_INTERP_CIC>(F, A, q, err, &lc);
         }
+        __syncwarp();
       }
+      for (int st = seg_len - 1; st >= 0; --st) {
+        if (st < len && alive) {
+          if (!reverse_step_mixed<Grav>(F, A, ys[st], r.eta_stop, yb, &lc, sc, R, err)) alive = false;
+        }
+        __syncwarp();
+      }
+    }
+    // 4. the initial wave vector k = n sqrt((1 + 2 phi_o)/(1 - 2 phi_o)) depends on phi_o
+    if (alive && Grav) {
+      const double nd[3] = {__ldg(&dirs[ray]), __ldg(&dirs[n + ray]), __ldg(&dirs[2 * n + ray])};
+      const double po = r.phi_o;
+      const double kn = sqrt((1.0 + 2.0 * po) / (1.0 - 2.0 * po));
+      const double phib =
+          (yb[5] * nd[0] + yb[6] * nd[1] + yb[7] * nd[2]) * 2.0 / (kn * (1.0 - 2.0 * po) * (1.0 - 2.0 * po));
+      scatter_observer(F, R, r.xo, phib, err);
     }
     acc_flush(F, R, sc);
-    ray = -1;
   }
 }
 

@@ -253,12 +253,13 @@ __device__ __forceinline__ bool cic_rows(const DevField& F, int l, const long lo
   return true;
 }
 
-// CIC (Eq. 8) gather at level l around lower corner i0 with in-cell fractions f, for the
-// two bracketing slices s, s+1 (or slice 0 when S = 1): out[0..3] at slice s, out[4..7] at
-// slice s+1.  Returns false if a neighbour is absent.
+// CIC (Eq. 8) gather at level l around lower corner i0, for the two bracketing slices s, s+1 (or
+// slice 0 when S = 1): out[0..3] at slice s, out[4..7] at slice s+1.  w[d][b]: the weight along axis
+// d of the corner i0_d + b; corner c weighs w[0][c & 1] w[1][c >> 1 & 1] w[2][c >> 2 & 1].  Returns
+// false if a neighbour is absent.
 template <class T>
-__device__ __forceinline__ bool cic_gather(const DevField& F, int l, const long long* i0, const T* f, int s, T* out,
-                                          unsigned* err) {
+__device__ __forceinline__ bool cic_gather(const DevField& F, int l, const long long* i0, const T (*w)[2], int s,
+                                          T* out, unsigned* err) {
   using V = typename Vec4<T>::type;
   unsigned rows[8];
   if (!cic_rows(F, l, i0, rows, err)) return false;
@@ -269,39 +270,38 @@ __device__ __forceinline__ bool cic_gather(const DevField& F, int l, const long 
   for (int q = 0; q < 8; ++q) out[q] = (T)0;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const T wx = (c & 1) ? f[0] : (T)1 - f[0];
-    const T wy = (c & 2) ? f[1] : (T)1 - f[1];
-    const T wz = (c & 4) ? f[2] : (T)1 - f[2];
-    const T w = wx * wy * wz;
+    const T wc = w[0][c & 1] * w[1][(c >> 1) & 1] * w[2][(c >> 2) & 1];
     const V* rc = rec + (size_t)rows[c] * (size_t)S;
     const V r0 = ldg4(rc + s);
     const V r1 = ldg4(rc + s1);
-    out[0] += w * r0.x;
-    out[1] += w * r0.y;
-    out[2] += w * r0.z;
-    out[3] += w * r0.w;
-    out[4] += w * r1.x;
-    out[5] += w * r1.y;
-    out[6] += w * r1.z;
-    out[7] += w * r1.w;
+    out[0] += wc * r0.x;
+    out[1] += wc * r0.y;
+    out[2] += wc * r0.z;
+    out[3] += wc * r0.w;
+    out[4] += wc * r1.x;
+    out[5] += wc * r1.y;
+    out[6] += wc * r1.z;
+    out[7] += wc * r1.w;
   }
   return true;
 }
 
-// CIC at level l from coarse-cell coordinates u: i0 = floor(u 2^l - 1/2), f = remainder.
+// CIC at level l from coarse-cell coordinates u: U = u 2^l, lower corner i0 = floor(U - 1/2), and
+// the weights of Eq. (8) as defined, W = 1 - |r| with r = U - (centre of the corner cell).
 template <class T>
 __device__ __forceinline__ bool cic_level(const DevField& F, int l, const double* u, int s, T* out, unsigned* err) {
   const double sc = (double)(1ll << l);
   long long i0[3];
-  T f[3];
+  T w[3][2];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    double U = u[d] * sc - 0.5;
-    double fl = floor(U);
+    const double U = u[d] * sc;
+    const double fl = floor(U - 0.5);
     i0[d] = (long long)fl;
-    f[d] = (T)(U - fl);
+    w[d][0] = (T)(1.0 - fabs(U - (fl + 0.5)));
+    w[d][1] = (T)(1.0 - fabs(U - (fl + 1.5)));
   }
-  return cic_gather<T>(F, l, i0, f, s, out, err);
+  return cic_gather<T>(F, l, i0, (const T(*)[2])w, s, out, err);
 }
 
 // ----------------------------------------------------------------- NGP and TSC (Eqs. 7, 9)
@@ -368,15 +368,23 @@ __device__ __forceinline__ void tsc_weights(T t, T* w, T* dw) {
 // TSC gather at level l around cell c (t as in tsc_weights), slices s, s+1 as cic_gather; with
 // dout, dout[d][q] receives the derivative with respect to the level-l coordinate d.  R: record
 // precision, T: arithmetic.
+// wdef (if non-null): the weights along each axis, given (then t is not used and dout must be null).
 template <class R, class T = R>
 __device__ __forceinline__ bool tsc_gather(const DevField& F, int l, const long long* c, const T* t, int s, T* out,
-                                          unsigned* err, T (*dout)[8] = nullptr) {
+                                          unsigned* err, T (*dout)[8] = nullptr, const T (*wdef)[3] = nullptr) {
   using V = typename Vec4<R>::type;
   unsigned a[3][3], plo[3], oct[8];
   if (!tsc_octets(F, l, c, a, plo, oct, err)) return false;
   T w[3][3], dw[3][3];
+  if (wdef) {
 #pragma unroll
-  for (int d = 0; d < 3; ++d) tsc_weights<T>(t[d], w[d], dout ? dw[d] : nullptr);
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) w[d][m] = wdef[d][m];
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) tsc_weights<T>(t[d], w[d], dout ? dw[d] : nullptr);
+  }
   const V* rec = (const V*)F.rec[l];
   const int S = F.S;
   const int s1 = (S > 1) ? s + 1 : s;
@@ -395,11 +403,11 @@ __device__ __forceinline__ bool tsc_gather(const DevField& F, int l, const long 
         const V* rc = rec + (size_t)tsc_row(l, a, plo, oct, mx, my, mz) * (size_t)S;
         const V r0 = ldg4(rc + s), r1 = ldg4(rc + s1);
         const T rr[8] = {(T)r0.x, (T)r0.y, (T)r0.z, (T)r0.w, (T)r1.x, (T)r1.y, (T)r1.z, (T)r1.w};
-        const T wyz = w[1][my] * w[2][mz];
-        const T wgt = w[0][mx] * wyz;
+        const T wgt = w[0][mx] * w[1][my] * w[2][mz];
 #pragma unroll
         for (int q = 0; q < 8; ++q) out[q] += wgt * rr[q];
         if (dout) {
+          const T wyz = w[1][my] * w[2][mz];
           const T d0 = dw[0][mx] * wyz, d1 = w[0][mx] * dw[1][my] * w[2][mz], d2 = w[0][mx] * w[1][my] * dw[2][mz];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
@@ -472,7 +480,20 @@ __device__ __forceinline__ bool interp_level(const DevField& F, int l, const dou
     t[d] = (T)(U - fl - 0.5);
   }
   if (ip == MT_INTERP_NGP) return ngp_gather<T>(F, l, c, s, out, err);
-  return tsc_gather<T>(F, l, c, t, s, out, err);
+  // the weights of Eq. (9) as defined, W(r) with r = U - (centre of the cell c + m - 1)
+  T wdef[3][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double U = u[d] * sc;
+    const double fl = (double)c[d];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const double r = U - ((fl + (double)(m - 1)) + 0.5);
+      const double a = fabs(r);
+      wdef[d][m] = (T)(a < 0.5 ? 0.75 - r * r : (a < 1.5 ? 0.5 * (1.5 - a) * (1.5 - a) : 0.0));
+    }
+  }
+  return tsc_gather<T, T>(F, l, c, t, s, out, err, nullptr, (const T(*)[3])wdef);
 }
 
 // Field at (x, eta): phi, grad phi and d phi/d eta, with the level fallback of Sect. 2.2
@@ -536,6 +557,8 @@ struct mt_octree {
   int num_sms;
   int launch_block;  // trace kernel threads per block (0: default 128)
   int launch_bps;    // trace kernel blocks per SM (0: as many as fit)
+  int ray_chunk;     // trace kernel: ray ids a warp claims per refill (0: default 32)
+  int staging;       // trace kernel, FP32 field, CIC: 0/1 per-lane shared-memory neighbourhood, 2 direct loads
 };
 
 namespace mt {

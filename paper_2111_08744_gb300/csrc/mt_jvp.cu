@@ -302,7 +302,7 @@ extern "C" mt_status mt_trace_rays_jvp(const mt_octree* tree, const mt_trace_par
   TraceArgs A;
   A.steps_per_cell = params->steps_per_cell;
   A.interp = params->interp;
-  A.pad = 0;
+  A.ray_chunk = 32;
   A.gravity_on = params->gravity_on ? 1 : 0;
   A.max_steps = params->max_steps;
   A.n_rays = n_rays;

@@ -176,7 +176,8 @@ __device__ __forceinline__ bool cic_int(const DevField& F, int l, const int* ic,
       f[d] = fl + 0.5f;
     }
   }
-  return cic_gather<float>(F, l, i0, f, s, v, err);
+  const float w[3][2] = {{1.0f - f[0], f[0]}, {1.0f - f[1], f[1]}, {1.0f - f[2], f[2]}};
+  return cic_gather<float>(F, l, i0, w, s, v, err);
 }
 
 // TSC (Eq. 9) at level l around cell c with the lane's neighbour cache: the rows of the 27 cells
@@ -188,7 +189,10 @@ template <bool WithD>
 __device__ __forceinline__ bool tsc_gather_cached(const DevField& F, int l, const long long* c, const float* t, int s,
                                                   float* out, unsigned* err, const LaneCache& lc,
                                                   float (*dout)[8] = nullptr) {
-  unsigned* rows = reinterpret_cast<unsigned*>(lc.rec);  // rows[m * stride], m = mx + 3 my + 9 mz
+  // the lane's 27 rows, interleaved with the other lanes' at 4-byte granularity over the record
+  // area (every kernel sets lc.rec = block base + threadIdx.x float4s, stride = threads per block):
+  // rows[m * stride], m = mx + 3 my + 9 mz, within the area's 64 x stride words
+  unsigned* rows = reinterpret_cast<unsigned*>(lc.rec - threadIdx.x) + threadIdx.x;
   const int4 key = make_int4((l << 8) | s, (int)c[0], (int)c[1], (int)c[2]);
   const int4 old = *lc.key;
   if (!(old.x == key.x && old.y == key.y && old.z == key.z && old.w == key.w)) {
@@ -223,11 +227,11 @@ __device__ __forceinline__ bool tsc_gather_cached(const DevField& F, int l, cons
         const float4* rc = rec + (size_t)rows[(mx + 3 * my + 9 * mz) * lc.stride] * (size_t)S;
         const float4 r0 = __ldg(rc + s), r1 = __ldg(rc + s1);
         const float rr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-        const float wyz = w[1][my] * w[2][mz];
-        const float wgt = w[0][mx] * wyz;
+        const float wgt = w[0][mx] * w[1][my] * w[2][mz];
 #pragma unroll
         for (int q = 0; q < 8; ++q) out[q] += wgt * rr[q];
         if constexpr (WithD) {
+          const float wyz = w[1][my] * w[2][mz];
           const float d0 = dw[0][mx] * wyz, d1 = w[0][mx] * dw[1][my] * w[2][mz], d2 = w[0][mx] * w[1][my] * dw[2][mz];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {

@@ -19,9 +19,9 @@
 
 namespace mt {
 
-// Ray ids a warp claims at a time: one lane's worth per lane.  Larger chunks leave warps holding
+// Ray ids a warp claims at a time (TraceArgs::ray_chunk, a multiple of 32; default 32, one lane's
+// worth per lane).  Larger chunks keep more of a warp's rays sky neighbours but leave warps holding
 // unstarted rays at the end of the queue (a tail with the rest of the GPU idle).
-constexpr int kRayChunk = 32;
 
 template <class T>
 __device__ void ray_init(const DevField& F, const DevCones& C, const double* __restrict__ dirs, long long n,
@@ -32,8 +32,10 @@ __device__ void ray_init(const DevField& F, const DevCones& C, const double* __r
 }
 
 // BS threads per block; the register budget (128 per thread) is the same for every block size.
-// IP: the interpolation scheme (MT_INTERP_*), fixed per instantiation.
-template <class T, int BS, int IP>
+// IP: the interpolation scheme (MT_INTERP_*), fixed per instantiation.  Staged (FP32 fields): each
+// ray's CIC neighbourhood (TSC: its 27 neighbour rows) is staged in shared memory; otherwise the
+// records are read through L1 at every stage.
+template <class T, int BS, int IP, bool Staged = true>
 __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCones C, const double* __restrict__ dirs,
                                                               OutPtrs O, TraceArgs A, unsigned long long* ws) {
   unsigned* err = (unsigned*)(ws + 1);
@@ -47,8 +49,9 @@ __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCone
   lc.key = (int4*)(smem + 16 * BS) + threadIdx.x;
   lc.stride = BS;
   lc.loc = (int4*)(smem + 16 * BS) + BS + threadIdx.x;
-  if (sizeof(T) == 4) *lc.loc = make_int4(0, 0, 0, -1);
-  const LaneCache* lcp = sizeof(T) == 4 ? &lc : nullptr;
+  if (sizeof(T) == 4 && Staged) *lc.loc = make_int4(0, 0, 0, -1);
+  const LaneCache* lcp = (sizeof(T) == 4 && Staged) ? &lc : nullptr;
+  const unsigned long long chunk = (unsigned long long)A.ray_chunk;
   RayState r;
   long long ray = -1;
   bool exhausted = false;
@@ -63,14 +66,14 @@ __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCone
       const int from_pool = k < pool_left ? k : pool_left;
       unsigned long long fresh = 0;
       if (k > from_pool) {
-        if ((int)lane == leader) fresh = atomicAdd(ws, (unsigned long long)kRayChunk);
+        if ((int)lane == leader) fresh = atomicAdd(ws, chunk);
         fresh = __shfl_sync(0xffffffffu, fresh, leader);
       }
       const int rank = __popc(m & ((1u << lane) - 1u));
       const unsigned long long pick = rank < from_pool ? pool + rank : fresh + (rank - from_pool);
       if (k > from_pool) {
         pool = fresh + (k - from_pool);
-        pool_left = kRayChunk - (k - from_pool);
+        pool_left = (int)chunk - (k - from_pool);
       } else {
         pool += k;
         pool_left -= k;
@@ -97,39 +100,51 @@ __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCone
   }
 }
 
-// Dynamic shared memory of trace_kernel<T, BS>: the mixed path's per-thread neighbourhood cache and
-// last locate answer (288 B per thread).
-template <class T, int BS>
+// Dynamic shared memory of trace_kernel<T, BS, IP, Staged>: the mixed path's per-thread neighbourhood
+// cache and last locate answer (288 B per thread).
+template <class T, int BS, bool Staged>
 constexpr size_t trace_smem() {
-  return sizeof(T) == 4 ? (size_t)BS * (16 * sizeof(float4) + 2 * sizeof(int4)) : 0;
+  return (sizeof(T) == 4 && Staged) ? (size_t)BS * (16 * sizeof(float4) + 2 * sizeof(int4)) : 0;
 }
 
-template <class T, int BS, int IP>
+template <class T, int BS, int IP, bool Staged>
 int blocks_per_sm() {
   static int cached = -1;
   if (cached < 0) {
-    const size_t sm = trace_smem<T, BS>();
+    const size_t sm = trace_smem<T, BS, Staged>();
     if (sm > 48 * 1024)
-      cudaFuncSetAttribute(trace_kernel<T, BS, IP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(trace_kernel<T, BS, IP, Staged>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<T, BS, IP>, BS, sm) != cudaSuccess || b < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<T, BS, IP, Staged>, BS, sm) != cudaSuccess ||
+        b < 1)
       b = 1;
     cached = b;
   }
   return cached;
 }
 
-template <class T, int BS, int IP>
+template <class T, int BS, int IP, bool Staged = true>
 void launch_trace_bs(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O,
                      const TraceArgs& A, cudaStream_t stream) {
-  int bps = blocks_per_sm<T, BS, IP>();
+  int bps = blocks_per_sm<T, BS, IP, Staged>();
   if (tree->launch_bps > 0 && tree->launch_bps < bps) bps = tree->launch_bps;
-  trace_kernel<T, BS, IP><<<tree->num_sms * bps, BS, trace_smem<T, BS>(), stream>>>(launch_field(tree, A), C, dirs,
-                                                                                    O, A, tree->ws);
+  trace_kernel<T, BS, IP, Staged><<<tree->num_sms * bps, BS, trace_smem<T, BS, Staged>(), stream>>>(
+      launch_field(tree, A), C, dirs, O, A, tree->ws);
 }
 
-// Launch shape: the octree's configuration (mt_set_launch_config), default 128 threads and as
-// many blocks per SM as fit.  NGP and TSC run with 128 threads per block.
+template <class T, bool Staged>
+void launch_trace_cic(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O,
+                      const TraceArgs& A, cudaStream_t stream) {
+  switch (tree->launch_block) {
+    case 64: launch_trace_bs<T, 64, MT_INTERP_CIC, Staged>(tree, C, dirs, O, A, stream); break;
+    case 256: launch_trace_bs<T, 256, MT_INTERP_CIC, Staged>(tree, C, dirs, O, A, stream); break;
+    default: launch_trace_bs<T, 128, MT_INTERP_CIC, Staged>(tree, C, dirs, O, A, stream); break;
+  }
+}
+
+// Launch shape: the octree's configuration (mt_set_launch_config, mt_set_trace_options), default 128
+// threads, as many blocks per SM as fit, the staged neighbourhood.  NGP and TSC run with 128 threads
+// per block, staged.
 template <class T>
 void launch_trace(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O, const TraceArgs& A,
                   cudaStream_t stream) {
@@ -141,11 +156,13 @@ void launch_trace(const mt_octree* tree, const DevCones& C, const double* dirs, 
     launch_trace_bs<T, 128, MT_INTERP_TSC>(tree, C, dirs, O, A, stream);
     return;
   }
-  switch (tree->launch_block) {
-    case 64: launch_trace_bs<T, 64, MT_INTERP_CIC>(tree, C, dirs, O, A, stream); break;
-    case 256: launch_trace_bs<T, 256, MT_INTERP_CIC>(tree, C, dirs, O, A, stream); break;
-    default: launch_trace_bs<T, 128, MT_INTERP_CIC>(tree, C, dirs, O, A, stream); break;
+  if constexpr (sizeof(T) == 4) {
+    if (tree->staging == 2) {
+      launch_trace_cic<T, false>(tree, C, dirs, O, A, stream);
+      return;
+    }
   }
+  launch_trace_cic<T, true>(tree, C, dirs, O, A, stream);
 }
 
 #ifdef MT_TU_FP64
@@ -209,7 +226,7 @@ extern "C" mt_status mt_trace_rays(const mt_octree* tree, const mt_trace_params*
   TraceArgs A;
   A.steps_per_cell = params->steps_per_cell;
   A.interp = params->interp;
-  A.pad = 0;
+  A.ray_chunk = tree->ray_chunk > 0 ? tree->ray_chunk : 32;
   A.gravity_on = params->gravity_on ? 1 : 0;
   A.max_steps = params->max_steps;
   A.n_rays = n_rays;
@@ -232,6 +249,14 @@ extern "C" mt_status mt_set_launch_config(mt_octree* tree, int32_t block_size, i
   if (blocks_per_sm < 0) return MT_ERR_INVALID_ARG;
   tree->launch_block = block_size;
   tree->launch_bps = blocks_per_sm;
+  return MT_OK;
+}
+extern "C" mt_status mt_set_trace_options(mt_octree* tree, int32_t ray_chunk, int32_t staging) {
+  if (!tree) return MT_ERR_INVALID_ARG;
+  if (ray_chunk != 0 && (ray_chunk < 32 || ray_chunk > 1024 || ray_chunk % 32 != 0)) return MT_ERR_INVALID_ARG;
+  if (staging < 0 || staging > 2) return MT_ERR_INVALID_ARG;
+  tree->ray_chunk = ray_chunk;
+  tree->staging = staging;
   return MT_OK;
 }
 #endif  // MT_TU_FP64

@@ -28,8 +28,8 @@ struct TraceArgs {
   int gravity_on;
   long long max_steps;
   long long n_rays;
-  int interp;  // MT_INTERP_*
-  int pad;
+  int interp;     // MT_INTERP_*
+  int ray_chunk;  // trace kernels: ray ids a warp claims per refill (a multiple of 32)
 };
 
 // The octree's field as a kernel argument, carrying the trace's interpolation scheme.

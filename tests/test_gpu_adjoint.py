@@ -285,3 +285,31 @@ def test_mixed_reverse_checkpoint_interval_does_not_change_gradients():
     for x, y in zip(a, b):
         # same arithmetic in every segment layout; only the FP64 atomics' order differs
         np.testing.assert_allclose(x, y, rtol=1e-9, atol=1e-9 * np.abs(x).max())
+
+
+def test_field_model_forward_on_the_gpu_matches_the_generator():
+    """mt_field_from_coarse_phi (phi_0 -> records of every level) against the generator's field model
+    (inputs.records_from_phi0) for a random phi_0, element by element; it is the transpose of the
+    pull-back: <records(v), rbar> - <records(0), rbar> = <v, pullback(rbar)>."""
+    import torch
+    from paper_2111_08744_gb300 import autograd as AG
+    from paper_2111_08744_gb300 import binding as B
+    w = _small()
+    rng = np.random.Generator(np.random.PCG64(61))
+    phi = rng.normal(size=(w.n_coarse,) * 3) * 1e-5
+    tc = AG.TraceContext(w)
+    got = [r.cpu().numpy() for r in tc.field_records(torch.from_numpy(phi).cuda())]
+    ref = I.records_from_phi0(w, phi)
+    for g, r in zip(got, ref):
+        np.testing.assert_allclose(g, r.records, rtol=1e-12, atol=1e-12 * np.abs(r.records).max())
+    # adjointness with the pull-back on the linear part
+    rbar = [rng.normal(size=l.records.shape) for l in w.levels]
+    key = tc.morton_index().cpu().numpy()
+    v_m = np.empty(key.size)
+    v_m[key] = phi.ravel()
+    lin = [g - b.cpu().numpy() for g, b in zip(got, tc._base)]
+    lhs = sum((a * b).sum() for a, b in zip(lin, rbar))
+    tree = tc._geom
+    pb = B.pullback_coarse_phi(tree, [torch.from_numpy(x).cuda() for x in rbar], w.slice_weight, w.n_coarse)
+    rhs = float((pb.cpu().numpy() * v_m).sum())
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), abs(rhs))
