@@ -87,6 +87,10 @@ def _load():
             lib.orc_trace_to_chi.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Level), ctypes.c_void_p,
                                              ctypes.c_int, ctypes.POINTER(_Params), ctypes.c_void_p, ctypes.c_int64,
                                              ctypes.c_void_p, ctypes.POINTER(_Out), ctypes.c_int]
+            lib.orc_trace_analytic.restype = ctypes.c_int
+            lib.orc_trace_analytic.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Level), ctypes.c_void_p,
+                                               ctypes.c_int, ctypes.POINTER(_Params), ctypes.c_void_p,
+                                               ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(_Out), ctypes.c_int]
             lib.orc_sample.restype = ctypes.c_int
             lib.orc_sample.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Level), ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
@@ -140,12 +144,14 @@ def _interp(interp):
 
 
 def trace(w, dirs=None, levels=None, gravity_on=True, max_steps=10_000_000, n_threads=None, ray_begin=None,
-          interp="cic", chi_stop=None):
+          interp="cic", chi_stop=None, analytic=None):
     """Trace rays of workload `w` (optionally other directions / a subset). Returns a dict of arrays.
 
     interp: "cic" (Eq. 8), "ngp" (Eq. 7) or "tsc" (Eq. 9), each with the level fallback of Sect. 2.2.
     chi_stop: per-ray comoving distances [N]: stop on the sphere |x - x_o| = chi_stop (the geodesic
     finder's criterion, Sect. 2.5) instead of the iso-eta surface of z_max.
+    analytic: (A, k_x, k_y, k_z): trace through phi = A sin(k . x) (exact, static) instead of the
+    records (a smooth field for integration-order tests; the octree still sets the step size).
 
     Besides the per-ray outputs of the method, "tie" is the smallest margin of any index
     decision along the ray: the distance (in cell units) of a floor() argument to the
@@ -168,7 +174,12 @@ def trace(w, dirs=None, levels=None, gravity_on=True, max_steps=10_000_000, n_th
     out.update({k: np.zeros(n, dtype=np.int32) for k in _OUT_I32})
     out["tie"] = np.ones(n)
     o = _Out(**{k: _ptr(v) for k, v in out.items()})
-    if chi_stop is None:
+    if analytic is not None:
+        an = np.ascontiguousarray(analytic, dtype=np.float64)
+        rc = lib.orc_trace_analytic(ctypes.byref(m.grid), m.levels, _ptr(m.bg), int(m.bg.shape[0]),
+                                    ctypes.byref(m.params), _ptr(d), n, _ptr(an), ctypes.byref(o),
+                                    int(n_threads or default_threads()))
+    elif chi_stop is None:
         rc = lib.orc_trace(ctypes.byref(m.grid), m.levels, _ptr(m.bg), int(m.bg.shape[0]), ctypes.byref(m.params),
                            _ptr(d), n, ctypes.byref(o), int(n_threads or default_threads()))
     else:

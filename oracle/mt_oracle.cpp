@@ -151,6 +151,9 @@ struct Field {
   bool periodic;
   const double* seta;
   const orc_level* lv;
+  // analytic potential phi = A sin(k . x), static (test mode: (A, k_x, k_y, k_z), k a multiple of
+  // 2 pi / box per axis so that it is periodic); NULL: the octree's records
+  const double* analytic = nullptr;
 
   int64_t n_at(int l) const { return (int64_t)nc << l; }
   double dx(int l) const { return box / (double)n_at(l); }
@@ -286,6 +289,16 @@ struct Field {
               double* tie = nullptr) const {
     int lf = finest(u, tie);
     if (lf < 0) return false;
+    if (analytic) {
+      // exact phi and grad phi at x = u dx_0 (the wrapped position; the field is periodic in the box)
+      double arg = 0.0;
+      for (int d = 0; d < 3; ++d) arg += analytic[1 + d] * (u[d] * dx(0));
+      *phi = analytic[0] * std::sin(arg);
+      for (int d = 0; d < 3; ++d) grad[d] = analytic[0] * analytic[1 + d] * std::cos(arg);
+      *phi_eta = 0.0;
+      if (lev_used) *lev_used = lf;
+      return true;
+    }
     double vals[64][4];
     int l = lf;
     for (; l >= 0; --l) {
@@ -607,10 +620,11 @@ int orc_sample(const orc_grid* g, const orc_level* lv, const double* pts /*[3][n
 
 static int trace_rays_impl(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n, const orc_params* p,
                     const double* dirs /*[3][N]*/, int64_t n_rays, const double* chi_stop, orc_out* o,
-                    int n_threads) {
+                    int n_threads, const double* analytic = nullptr) {
   if (!keys_sorted(g, lv)) return 4;
   if (p->interp < INTERP_CIC || p->interp > INTERP_TSC) return 5;
   Tracer t = make_tracer(g, lv, bg, bg_n, p);
+  t.f.analytic = analytic;
   std::vector<double> es(p->n_cones);
   for (int c = 0; c < p->n_cones; ++c) es[c] = chi_stop ? bg[0] : t.bg.eta_stop(p->z_max[c]);
   parallel_for(n_rays, n_threads, [&](int64_t i) {
@@ -760,6 +774,14 @@ int orc_infinitesimal(const orc_grid* g, const orc_level* lv, const double* bg, 
 int orc_trace(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n, const orc_params* p,
               const double* dirs /*[3][N]*/, int64_t n_rays, orc_out* o, int n_threads) {
   return trace_rays_impl(g, lv, bg, bg_n, p, dirs, n_rays, nullptr, o, n_threads);
+}
+
+// Rays through the analytic potential phi = A sin(k . x) (analytic = (A, k_x, k_y, k_z)) instead of the
+// records: the same integrator with an exactly smooth field (a test of the integration order with the
+// gravitational terms); the octree still sets the levels and so the step size.
+int orc_trace_analytic(const orc_grid* g, const orc_level* lv, const double* bg, int bg_n, const orc_params* p,
+                       const double* dirs, int64_t n_rays, const double* analytic, orc_out* o, int n_threads) {
+  return trace_rays_impl(g, lv, bg, bg_n, p, dirs, n_rays, nullptr, o, n_threads, analytic);
 }
 
 // Rays stopped at the comoving distances chi_stop[i] (the geodesic finder's iso-chi surface, Sect. 2.5).

@@ -107,21 +107,27 @@ __device__ __forceinline__ bool cic_int_cached(const DevField& F, int l, const i
   const int4 key = make_int4((l << 8) | s, i0[0], i0[1], i0[2]);
   const int4 old = *lc.key;
   const bool hit = old.x == key.x && old.y == key.y && old.z == key.z && old.w == key.w;
+  // the miss path rejoins before the gather (no early exit from inside it): the lanes that staged a
+  // new neighbourhood and those that reuse theirs then run the weights and the gather together
+  bool ok = true;
   if (!hit) {
     const long long i0l[3] = {i0[0], i0[1], i0[2]};
     unsigned rows[8];
-    if (!cic_rows(F, l, i0l, rows, err)) return false;
-    const float4* rec = (const float4*)F.rec[l];
-    const int S = F.S;
-    const int s1 = (S > 1) ? s + 1 : s;
+    ok = cic_rows(F, l, i0l, rows, err);
+    if (ok) {
+      const float4* rec = (const float4*)F.rec[l];
+      const int S = F.S;
+      const int s1 = (S > 1) ? s + 1 : s;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const float4* rc = rec + (size_t)rows[c] * (size_t)S;
-      lc.rec[(2 * c) * lc.stride] = __ldg(rc + s);
-      lc.rec[(2 * c + 1) * lc.stride] = __ldg(rc + s1);
+      for (int c = 0; c < 8; ++c) {
+        const float4* rc = rec + (size_t)rows[c] * (size_t)S;
+        lc.rec[(2 * c) * lc.stride] = __ldg(rc + s);
+        lc.rec[(2 * c + 1) * lc.stride] = __ldg(rc + s1);
+      }
+      *lc.key = key;
     }
-    *lc.key = key;
   }
+  if (!ok) return false;
 #pragma unroll
   for (int q = 0; q < 8; ++q) v[q] = 0.0f;
   if constexpr (WithD) {
