@@ -40,18 +40,20 @@ FIELD_BYTES_BY_SCHEME = {"ngp": 4 * 1 * 16 * 2, "cic": FIELD_BYTES_PER_STEP, "ts
 # (its sources with comments removed) at capture time; reported only while that code is unchanged.
 #   dram_bytes_per_launch: dram__bytes_read.sum + dram__bytes_write.sum of one full launch (a
 #       single-pass capture of the benchmark command);
-#   per_rk4_step: smsp__inst_executed.sum (warp instructions) and smsp__inst_executed_pipe_fp64.sum
-#       (warp instructions on the FP64 pipe) divided by the RK4 steps of the captured launch (the
-#       65,536-ray profiling launch, --set full);
-#   pct: the same capture's sm__pipe_fp64_cycles_active, smsp__issue_active, sm__warps_active
-#       (percent of peak) and active lanes per instruction.
+#   per_rk4_step, from the --set full capture of the 65,536-ray profiling launch (158,966,573 RK4
+#       steps): warp_inst = smsp__inst_executed.sum / steps; fp64_lane_slots = FP64-pipe lane slots
+#       occupied per step = sm__pipe_fp64_cycles_active (fraction of active cycles) x
+#       sm__cycles_active.sum x 2 lanes per cycle (the pipe's peak, 2 DFMA lanes per cycle per SM) / steps;
+#   pct: that capture's percentages of peak.
 TRACE_KERNEL_SOURCES = ["include/mt.h", "paper_2111_08744_gb300/csrc/mt_internal.cuh",
                         "paper_2111_08744_gb300/csrc/mt_mixed.cuh", "paper_2111_08744_gb300/csrc/mt_trace_device.cuh",
                         "paper_2111_08744_gb300/csrc/mt_trace.cu"]
-NCU_RECORD = {"sources_sha256": "",
-              "dram_bytes_per_launch": None,
-              "per_rk4_step": {"warp_inst": None, "fp64_warp_inst": None},
-              "pct": {}}
+NCU_RECORD = {"sources_sha256": "a4bc7eae4c110edd543c4d2d0336a8712a9627657c714a5e4b9172d14efe14d6",
+              "dram_bytes_per_launch": 57933815552 + 966122752,
+              "per_rk4_step": {"warp_inst": 131.264, "fp64_lane_slots": 69.286},
+              "pct": {"fp64_pipe": 43.53, "fp64_pipe_busiest_sm": 51.90, "issue_active": 43.04,
+                      "warps_active": 19.83, "lanes_per_inst": 15.59, "dram_throughput": 2.45,
+                      "l2_hit_rate": 49.25}}
 SMS, SCHEDULERS_PER_SM = 152, 4
 
 
@@ -90,14 +92,14 @@ def measured_traffic():
 
 def roofline(total_steps, ms, sm_mhz, fp64_fma_per_s, hbm_gbs, field_bytes, record, peaks_source):
     """Roofline of the trace kernel.  The binding resource is arithmetic issue, not HBM (the field
-    gathers are served by shared memory, L1 and L2): the headline is the FP64 pipe -- FP64 warp
-    instructions per RK4 step (ncu) x 32 lanes x RK4 steps per second (CUDA events), against the FP64
-    FMA lane rate measured on this GPU by mt_probe_fp64_fma_rate -- with the issue-slot fraction, the
+    gathers are served by shared memory, L1 and L2): the headline is the FP64 pipe -- the FP64 lane
+    slots it occupies per RK4 step (ncu) x RK4 steps per second (CUDA events), against the FP64 FMA
+    lane rate measured on this GPU by mt_probe_fp64_fma_rate -- with the issue-slot fraction, the
     DRAM fraction (ncu traffic) and the algorithmic field bandwidth ("effective") beside it."""
     t = ms * 1e-3
     steps_per_s = total_steps / t
     eff = field_bytes * steps_per_s / 1e9
-    out = {"bound": "alu", "unit": "G FP64 lane-ops/s", "achieved": None, "peak": fp64_fma_per_s / 1e9,
+    out = {"bound": "alu", "unit": "G FP64 lane-slots/s", "achieved": None, "peak": fp64_fma_per_s / 1e9,
            "frac": None, "traffic": None, "kernel": "trace_kernel<float>",
            "peak_source": "mt_probe_fp64_fma_rate, measured in this run (of measured)",
            "limiter": "latency-bound issue: FP64 pipe and issue slots share the time, DRAM is not the limit",
@@ -108,8 +110,8 @@ def roofline(total_steps, ms, sm_mhz, fp64_fma_per_s, hbm_gbs, field_bytes, reco
         out["ncu_record"] = "stale: the trace kernel changed since the last ncu capture"
         return out
     per = record["per_rk4_step"]
-    if per.get("fp64_warp_inst"):
-        ach = per["fp64_warp_inst"] * 32 * steps_per_s
+    if per.get("fp64_lane_slots"):
+        ach = per["fp64_lane_slots"] * steps_per_s
         out["achieved"] = ach / 1e9
         out["frac"] = ach / fp64_fma_per_s
     if per.get("warp_inst") and sm_mhz:

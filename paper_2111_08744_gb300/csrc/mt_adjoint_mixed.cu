@@ -362,6 +362,13 @@ __global__ void __launch_bounds__(kAdjMBlock) count_mixed_kernel(DevField F, Dev
   }
 }
 
+// The mixed step, out of line: the forward pass and the segment recompute of the reverse sweep share
+// one copy of its code (two inlined copies beside the reverse step outgrow the instruction cache).
+__device__ __noinline__ bool step_out_of_line(const DevField& F, const TraceArgs& A, RayState& r, unsigned* err,
+                                              const LaneCache* lc) {
+  return ray_step_mixed<MT_INTERP_CIC>(F, A, r, err, lc);
+}
+
 // Scatter the cotangent phib of phi at the observer (the initial wave vector depends on it) onto the
 // CIC records ray_start sampled there (FP64 coordinates, FP32 weights, the slice bracket of eta_o).
 __device__ void scatter_observer(const DevField& F, const RecBarM& R, const double* xo, double phib, unsigned* err) {
@@ -460,7 +467,7 @@ __global__ void __launch_bounds__(kAdjMBlock, 3) adjoint_mixed_kernel(DevField F
             for (int i = 0; i < 8; ++i) cp[i] = r.y[i];
           }
         }
-        if (fwd && ray_step_mixed<MT_INTERP_CIC>(F, A, r, err, &lc)) fwd = false;
+        if (fwd && step_out_of_line(F, A, r, err, &lc)) fwd = false;
       }
     }
     if (have) ray_finish<float>(F, A, r, ray, n, O, err);
@@ -500,7 +507,7 @@ __global__ void __launch_bounds__(kAdjMBlock, 3) adjoint_mixed_kernel(DevField F
       for (int st = 0; st < seg_len; ++st) {
         if (st < len) {
           for (int i = 0; i < 8; ++i) ys[st][i] = q.y[i];
-          if (st + 1 < len) ray_step_mixed<MT_INTERP_CIC>(F, A, q, err, &lc);
+          if (st + 1 < len) step_out_of_line(F, A, q, err, &lc);
         }
         __syncwarp();
       }

@@ -42,12 +42,12 @@ def test_comment_stripping_keeps_strings():
 
 def test_roofline_arithmetic():
     rec = {"sources_sha256": "x", "dram_bytes_per_launch": 50e9,
-           "per_rk4_step": {"warp_inst": 100.0, "fp64_warp_inst": 2.0}, "pct": {}}
+           "per_rk4_step": {"warp_inst": 100.0, "fp64_lane_slots": 64.0}, "pct": {}}
     r = bench.roofline(1e9, 500.0, 2000.0, 5e11, 6700.0, 1024, rec, "test")
     steps_per_s = 1e9 / 0.5
     assert r["bound"] == "alu"
-    assert abs(r["achieved"] - 2.0 * 32 * steps_per_s / 1e9) < 1e-9
-    assert abs(r["frac"] - 2.0 * 32 * steps_per_s / 5e11) < 1e-12
+    assert abs(r["achieved"] - 64.0 * steps_per_s / 1e9) < 1e-9
+    assert abs(r["frac"] - 64.0 * steps_per_s / 5e11) < 1e-12
     assert abs(r["issue"]["frac"] - 100.0 * steps_per_s / (152 * 4 * 2000e6)) < 1e-12
     assert abs(r["dram"]["achieved_GBs"] - 100.0) < 1e-9 and r["traffic"] == 50e9
     assert abs(r["hbm_effective"]["achieved_GBs"] - 1024 * steps_per_s / 1e9) < 1e-6
