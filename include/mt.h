@@ -66,13 +66,15 @@ typedef struct mt_octree mt_octree; /* opaque, library-owned */
 /*
  * Grid description (Sect. 2.1).  Level l has N_l = n_coarse * 2^l cells per
  * axis of size dx_l = box / N_l; n_coarse must be a power of two and
- * N_{n_levels} <= 2^21.  Cell (i, j, k) of level l has the Morton key with
- * bit 3b = bit b of i, bit 3b+1 = bit b of j, bit 3b+2 = bit b of k, so the
- * 8 children of a cell with key K have keys 8K .. 8K+7.
+ * N_{n_levels} <= 2^21, and no level may hold more than 2^32 cells (the
+ * kernels address records by 32-bit rows, so N_0 <= 1024).  Cell (i, j, k)
+ * of level l has the Morton key with bit 3b = bit b of i, bit 3b+1 = bit b
+ * of j, bit 3b+2 = bit b of k, so the 8 children of a cell with key K have
+ * keys 8K .. 8K+7.
  */
 typedef struct {
   double box;               /* comoving side of the (periodic) box, > 0 */
-  int32_t n_coarse;         /* N_0, power of two in [1, 2^20] */
+  int32_t n_coarse;         /* N_0, power of two in [1, 1024] */
   int32_t n_levels;         /* refined levels, 0 .. MT_MAX_LEVELS */
   int32_t periodic;         /* 1: positions wrap into the box; 0: rays stop at the box edge */
   int32_t n_slices;         /* time slices, 1 .. MT_MAX_SLICES */

@@ -172,6 +172,8 @@ extern "C" mt_status mt_build_octree(const mt_grid_desc* grid, const mt_level_da
   }
   const long long n0 = (long long)nc * nc * nc;
   if (levels[0].count != n0 || !levels[0].records) return MT_ERR_INVALID_ARG;
+  for (int l = 0; l <= L; ++l)  // the kernels address a level's records by 32-bit row
+    if (levels[l].count > (1ll << 32)) return MT_ERR_INVALID_ARG;
   for (int l = 1; l <= L; ++l) {
     if (levels[l].count < 0 || (levels[l].count & 7) != 0) return MT_ERR_NOT_FULL_TREE;
     if (levels[l].count > 0 && (!levels[l].keys || !levels[l].records)) return MT_ERR_INVALID_ARG;
