@@ -38,22 +38,25 @@ FIELD_BYTES_BY_SCHEME = {"ngp": 4 * 1 * 16 * 2, "cic": FIELD_BYTES_PER_STEP, "ts
 
 # ncu record of trace_kernel<float> on the benchmark workload, with the SHA-256 of the kernel's code
 # (its sources with comments removed) at capture time; reported only while that code is unchanged.
-#   dram_bytes_per_launch: dram__bytes_read.sum + dram__bytes_write.sum of one full launch (a
-#       single-pass capture of the benchmark command);
-#   per_rk4_step, from the --set full capture of the 65,536-ray profiling launch (158,966,573 RK4
-#       steps): warp_inst = smsp__inst_executed.sum / steps; fp64_lane_slots = FP64-pipe lane slots
-#       occupied per step = sm__pipe_fp64_cycles_active (fraction of active cycles) x
-#       sm__cycles_active.sum x 2 lanes per cycle (the pipe's peak, 2 DFMA lanes per cycle per SM) / steps;
-#   pct: that capture's percentages of peak.
+# Every figure comes from single-pass captures of full benchmark launches (1,907,632,740 RK4 steps),
+# one metric per capture:
+#   dram_bytes_per_launch: dram__bytes_read.sum + dram__bytes_write.sum;
+#   per_rk4_step: warp_inst = smsp__inst_executed.sum / steps; fp64_lane_slots = FP64-pipe lane slots
+#       occupied per step = sm__pipe_fp64_cycles_active.sum x 2 lanes per cycle (the pipe's peak, 2
+#       DFMA lanes per cycle per SM; a warp instruction holds it 16 cycles) / steps;
+#   pct: fp64_pipe = sm__pipe_fp64_cycles_active.sum / sm__cycles_active.sum; issue_active =
+#       smsp__issue_active.sum / (4 x sm__cycles_active.sum); warps_active = sm__warps_active.sum /
+#       (64 x sm__cycles_active.sum); lanes_per_inst = smsp__thread_inst_executed.sum /
+#       smsp__inst_executed.sum; dram_throughput = the DRAM bytes over the launch time against the
+#       measured copy rate; l2_hit_rate from the --set full capture of a 65,536-ray launch.
 TRACE_KERNEL_SOURCES = ["include/mt.h", "paper_2111_08744_gb300/csrc/mt_internal.cuh",
                         "paper_2111_08744_gb300/csrc/mt_mixed.cuh", "paper_2111_08744_gb300/csrc/mt_trace_device.cuh",
                         "paper_2111_08744_gb300/csrc/mt_trace.cu"]
-NCU_RECORD = {"sources_sha256": "a4bc7eae4c110edd543c4d2d0336a8712a9627657c714a5e4b9172d14efe14d6",
+NCU_RECORD = {"sources_sha256": "55db78c4264d2c3ea744afeb9f4a1fad97f019a8b54eb53bf1b4b0a0614e1a85",
               "dram_bytes_per_launch": 57933815552 + 966122752,
-              "per_rk4_step": {"warp_inst": 131.264, "fp64_lane_slots": 69.286},
-              "pct": {"fp64_pipe": 43.53, "fp64_pipe_busiest_sm": 51.90, "issue_active": 43.04,
-                      "warps_active": 19.83, "lanes_per_inst": 15.59, "dram_throughput": 2.45,
-                      "l2_hit_rate": 49.25}}
+              "per_rk4_step": {"warp_inst": 130.640, "fp64_lane_slots": 69.441},
+              "pct": {"fp64_pipe": 51.47, "issue_active": 48.72, "warps_active": 24.00, "lanes_per_inst": 15.66,
+                      "dram_throughput": 2.13, "l2_hit_rate": 49.25}}
 SMS, SCHEDULERS_PER_SM = 152, 4
 
 

@@ -6,11 +6,11 @@
 // Per ray (one lane; a warp takes 32 consecutive ray ids at a time and runs their phases in lockstep):
 //   1. integrate forward with the mixed step, keeping the FP64 state every `checkpoint_every` steps;
 //   2. form the cotangent of the final state from dL/dxi, xi = x - (k/k0)(eta - eta_stop);
-//   3. for each segment, last to first: recompute its states from the checkpoint, then reverse each
-//      step: a plain pass over the 4 stages gives the stage offsets and right-hand sides, then the
-//      stages from the last to the first are evaluated again with the derivatives of the CIC
-//      interpolant (FP32) and their transposed Jacobians applied in FP32 to the stage cotangents,
-//      while the state's cotangent accumulates in FP64.  The parts of the step that are linear in
+//   3. for each segment, last to first: recompute its steps from the checkpoint, keeping each step's
+//      start state and stage data (the stage wave-vector offsets, right-hand sides and step size),
+//      then reverse each step: the stages from the last to the first are evaluated again with the
+//      derivatives of the CIC interpolant (FP32) and their transposed Jacobians applied in FP32 to
+//      the stage cotangents, while the state's cotangent accumulates in FP64.  The parts of the step that are linear in
 //      the step-start state (x += h k, eta += h k0, and the step size's dependence on k0 and eta)
 //      are applied in FP64, as in the forward step;
 //   4. the cotangents of grad phi and phi_eta at each stage go to the stage's 8 CIC records of both
@@ -156,12 +156,12 @@ __device__ __forceinline__ void stage_adjoint_mixed(const StageF& sf, float k0, 
   *pebar = dpebar;
 }
 
-// Reverse of one mixed step from the step-start state y (FP64 x[3], eta, k0, k[3]): yb holds the
-// cotangent of the step's end state on entry and of its start state on return.  The forward
-// quantities are recomputed exactly as ray_step_mixed computes them.  False if a stage left a
-// non-periodic domain (cannot happen on a ray that ended with MT_RAY_OK).
+// Reverse of one mixed step from the step-start state y (FP64 x[3], eta, k0, k[3]) and the step's
+// stage data `rec` (recorded by ray_step_mixed when the segment was recomputed): yb holds the
+// cotangent of the step's end state on entry and of its start state on return.  False if a stage
+// left a non-periodic domain (cannot happen on a ray that ended with MT_RAY_OK).
 template <bool Grav>
-__device__ bool reverse_step_mixed(const DevField& F, const TraceArgs& A, const double* y, double eta_stop,
+__device__ bool reverse_step_mixed(const DevField& F, const TraceArgs& A, const double* y, const float* rec,
                                    double* yb, const LaneCache* lc, const ScatterAcc& sc, const RecBarM& R,
                                    unsigned* err) {
   MixedStep B;
@@ -169,51 +169,12 @@ __device__ bool reverse_step_mixed(const DevField& F, const TraceArgs& A, const 
   const double eta = y[3];
   const float k0s = (float)y[4];
   const float ks[3] = {(float)y[5], (float)y[6], (float)y[7]};
-  // forward pass over the stages (as ray_step_mixed): each stage's wave-vector offset from the step
-  // start (its wave vector is then k + offset, as there) and its right-hand side
-  float okk[4][4], Kk[4][4];  // [stage][k0, k1, k2, k3] offsets and [stage][dk0, dk1, dk2, dk3]/dlambda
-  float h = 0.0f;
-  bool last = false;
-  {
-    float offx[3] = {0.0f, 0.0f, 0.0f}, offe = 0.0f, offk0 = 0.0f, offk[3] = {0.0f, 0.0f, 0.0f};
-    // one copy of the stage code (an unrolled kernel outgrows the instruction cache)
-#pragma unroll 1
-    for (int st = 0; st < 4; ++st) {
-      const float k0v = k0s + offk0;
-      const float kv[3] = {ks[0] + offk[0], ks[1] + offk[1], ks[2] + offk[2]};
-      float Kk0, Kkv[3], KI, Ks;
-      int lf = 0;
-      if (!rhs_mixed<false, MT_INTERP_CIC>(F, Grav, B, eta, offx, offe, k0v, kv, &Kk0, Kkv, &KI, &Ks,
-                                           st == 0 ? &lf : nullptr, err, lc))
-        return false;
-      if (st == 0) {
-        const float dxl = F.dx0_f / (float)(1 << lf);
-        h = dxl / ((float)A.steps_per_cell * fabsf(k0s));
-        const float d = (float)(eta_stop - eta);
-        if (k0s * h <= d) {
-          h = d / k0s;
-          last = true;
-        }
-      }
-      okk[st][0] = offk0;
-      okk[st][1] = offk[0];
-      okk[st][2] = offk[1];
-      okk[st][3] = offk[2];
-      Kk[st][0] = Kk0;
-      Kk[st][1] = Kkv[0];
-      Kk[st][2] = Kkv[1];
-      Kk[st][3] = Kkv[2];
-      const float c = (st == 2 ? 1.0f : 0.5f) * h;
-      offx[0] = c * kv[0];
-      offx[1] = c * kv[1];
-      offx[2] = c * kv[2];
-      offe = c * k0v;
-      offk0 = c * Kk0;
-      offk[0] = c * Kkv[0];
-      offk[1] = c * Kkv[1];
-      offk[2] = c * Kkv[2];
-    }
-  }
+  // the stages' wave-vector offsets (k0, k) from the step start (stage st's wave vector is the step
+  // start's plus okk(st, .)) and their right-hand sides Kk(st, .) = (dk0, dk)/dlambda
+  const auto okk = [rec](int st, int i) { return rec[4 * st + i]; };
+  const auto Kk = [rec](int st, int i) { return rec[16 + 4 * st + i]; };
+  const float h = rec[32];
+  const bool last = rec[33] != 0.0f;
   // y' = y + h sum_j b_j K_j, K_j = (k + dk_j, k0 + dk0_j, Kk0_j, Kk_j) with the FP64 step-start k, k0
   // (x and eta advance by h k in FP64 and h sum_j b_j dk_j in FP32, as in ray_step_mixed): the
   // cotangents of the stage right-hand sides, and of h, whose step-start part is formed in FP64 (it
@@ -227,8 +188,8 @@ __device__ bool reverse_step_mixed(const DevField& F, const TraceArgs& A, const 
 #pragma unroll 1
   for (int st = 0; st < 4; ++st) {
     const float b = (st == 0 || st == 3) ? (1.0f / 6.0f) : (1.0f / 3.0f);
-    hbar_f += b * (ybf[0] * okk[st][1] + ybf[1] * okk[st][2] + ybf[2] * okk[st][3] + ybf[3] * okk[st][0] +
-                   ybf[4] * Kk[st][0] + ybf[5] * Kk[st][1] + ybf[6] * Kk[st][2] + ybf[7] * Kk[st][3]);
+    hbar_f += b * (ybf[0] * okk(st, 1) + ybf[1] * okk(st, 2) + ybf[2] * okk(st, 3) + ybf[3] * okk(st, 0) +
+                   ybf[4] * Kk(st, 0) + ybf[5] * Kk(st, 1) + ybf[6] * Kk(st, 2) + ybf[7] * Kk(st, 3));
   }
   // stages from the last to the first.  Stage j sits at y + a_{j-1} h K_{j-1}, so the cotangent of
   // K_j is b_j h yb' (the step's sum) plus a_j h times the cotangent of stage j + 1's state.
@@ -240,10 +201,10 @@ __device__ bool reverse_step_mixed(const DevField& F, const TraceArgs& A, const 
     const float a = st == 3 ? 1.0f : 0.5f;  // stage st sits at y + a h K_{st-1}
     float kp0 = 0.0f, kp[3] = {0.0f, 0.0f, 0.0f};  // wave vector of stage st - 1
     if (st > 0) {
-      kp0 = k0s + okk[st - 1][0];
-      kp[0] = ks[0] + okk[st - 1][1];
-      kp[1] = ks[1] + okk[st - 1][2];
-      kp[2] = ks[2] + okk[st - 1][3];
+      kp0 = k0s + okk(st - 1, 0);
+      kp[0] = ks[0] + okk(st - 1, 1);
+      kp[1] = ks[1] + okk(st - 1, 2);
+      kp[2] = ks[2] + okk(st - 1, 3);
       const float c = a * h;
       offx[0] = c * kp[0];
       offx[1] = c * kp[1];
@@ -255,8 +216,8 @@ __device__ bool reverse_step_mixed(const DevField& F, const TraceArgs& A, const 
     float Kb[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) Kb[i] = b * h * ybf[i] + (st < 3 ? an * h * tbn[i] : 0.0f);
-    const float k0v = k0s + okk[st][0];
-    const float kv[3] = {ks[0] + okk[st][1], ks[1] + okk[st][2], ks[2] + okk[st][3]};
+    const float k0v = k0s + okk(st, 0);
+    const float kv[3] = {ks[0] + okk(st, 1), ks[1] + okk(st, 2), ks[2] + okk(st, 3)};
     float Kk0, Kkv[3], KI, Ks;
     StageF sf;
     if (!rhs_mixed<true, MT_INTERP_CIC>(F, Grav, B, eta, offx, offe, k0v, kv, &Kk0, Kkv, &KI, &Ks, nullptr, err,
@@ -269,7 +230,8 @@ __device__ bool reverse_step_mixed(const DevField& F, const TraceArgs& A, const 
     for (int i = 0; i < 8; ++i) acc[i] += tbn[i];
     if (st > 0) {
       // Y_st = y + a h K_{st-1}, K_{st-1} = (k, k0, Kk0, Kk) of stage st - 1
-      const float Kprev[8] = {kp[0], kp[1], kp[2], kp0, Kk[st - 1][0], Kk[st - 1][1], Kk[st - 1][2], Kk[st - 1][3]};
+      const float Kprev[8] = {kp[0],         kp[1],         kp[2],         kp0,
+                              Kk(st - 1, 0), Kk(st - 1, 1), Kk(st - 1, 2), Kk(st - 1, 3)};
       float dot = 0.0f;
 #pragma unroll
       for (int i = 0; i < 8; ++i) dot += tbn[i] * Kprev[i];
@@ -363,10 +325,11 @@ __global__ void __launch_bounds__(kAdjMBlock) count_mixed_kernel(DevField F, Dev
 }
 
 // The mixed step, out of line: the forward pass and the segment recompute of the reverse sweep share
-// one copy of its code (two inlined copies beside the reverse step outgrow the instruction cache).
+// one copy of its code (inlined copies beside the reverse step outgrow the instruction cache); the
+// recompute records each step's stage data for the reverse step (rec null: no record).
 __device__ __noinline__ bool step_out_of_line(const DevField& F, const TraceArgs& A, RayState& r, unsigned* err,
-                                              const LaneCache* lc) {
-  return ray_step_mixed<MT_INTERP_CIC>(F, A, r, err, lc);
+                                              const LaneCache* lc, float* rec) {
+  return ray_step_mixed<MT_INTERP_CIC, true>(F, A, r, err, lc, rec);
 }
 
 // Scatter the cotangent phib of phi at the observer (the initial wave vector depends on it) onto the
@@ -432,6 +395,7 @@ __global__ void __launch_bounds__(kAdjMBlock, 3) adjoint_mixed_kernel(DevField F
   for (int j = 0; j < 64; ++j) sc.acc[j * sc.stride] = 0.0f;
   *sc.key = make_int4(-1, 0, 0, 0);
   double ys[kMaxSegmentM][8];
+  float rs[kMaxSegmentM][kStepRecordFloats];
   const unsigned lane = threadIdx.x & 31u;
   const long long n = A.n_rays;
   for (;;) {
@@ -467,7 +431,7 @@ __global__ void __launch_bounds__(kAdjMBlock, 3) adjoint_mixed_kernel(DevField F
             for (int i = 0; i < 8; ++i) cp[i] = r.y[i];
           }
         }
-        if (fwd && step_out_of_line(F, A, r, err, &lc)) fwd = false;
+        if (fwd && step_out_of_line(F, A, r, err, &lc, nullptr)) fwd = false;
       }
     }
     if (have) ray_finish<float>(F, A, r, ray, n, O, err);
@@ -507,13 +471,13 @@ __global__ void __launch_bounds__(kAdjMBlock, 3) adjoint_mixed_kernel(DevField F
       for (int st = 0; st < seg_len; ++st) {
         if (st < len) {
           for (int i = 0; i < 8; ++i) ys[st][i] = q.y[i];
-          if (st + 1 < len) step_out_of_line(F, A, q, err, &lc);
+          step_out_of_line(F, A, q, err, &lc, rs[st]);  // the last step's end state is not kept
         }
         __syncwarp();
       }
       for (int st = seg_len - 1; st >= 0; --st) {
         if (st < len && alive) {
-          if (!reverse_step_mixed<Grav>(F, A, ys[st], r.eta_stop, yb, &lc, sc, R, err)) alive = false;
+          if (!reverse_step_mixed<Grav>(F, A, ys[st], rs[st], yb, &lc, sc, R, err)) alive = false;
         }
         __syncwarp();
       }

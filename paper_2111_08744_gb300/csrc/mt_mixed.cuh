@@ -489,10 +489,16 @@ __device__ __forceinline__ bool mixed_begin(const DevField& F, const double* y, 
   return true;
 }
 
-// One mixed-precision RK4 step; state and status conventions as ray_step.
-template <int IP = MT_INTERP_CIC, class RayStateT, class TraceArgsT>
+// Stage data of one mixed step that its reverse needs (Record instances of ray_step_mixed): the
+// wave-vector offsets (k0, k) of the 4 stages from the step start, their right-hand sides
+// (dk0, dk)/dlambda, the step size and whether the step was the last.
+constexpr int kStepRecordFloats = 34;  // [0, 16) offsets, [16, 32) right-hand sides, 32: h, 33: last
+
+// One mixed-precision RK4 step; state and status conventions as ray_step.  Record: if rec is not
+// null it receives the step's stage data (kStepRecordFloats floats).
+template <int IP = MT_INTERP_CIC, bool Record = false, class RayStateT, class TraceArgsT>
 __device__ bool ray_step_mixed(const DevField& F, const TraceArgsT& A, RayStateT& r, unsigned* err,
-                               const LaneCache* lc = nullptr) {
+                               const LaneCache* lc = nullptr, float* rec = nullptr) {
   if (r.n_steps == 0 && !(r.y[3] > r.eta_stop)) return true;
   if (r.n_steps >= A.max_steps) {
     r.status = MT_RAY_MAX_STEPS;
@@ -532,6 +538,18 @@ __device__ bool ray_step_mixed(const DevField& F, const TraceArgsT& A, RayStateT
         last = true;
       }
     }
+    if constexpr (Record) {
+      if (rec) {
+        rec[4 * st] = offk0;
+        rec[4 * st + 1] = offk[0];
+        rec[4 * st + 2] = offk[1];
+        rec[4 * st + 3] = offk[2];
+        rec[16 + 4 * st] = Kk0;
+        rec[16 + 4 * st + 1] = Kk[0];
+        rec[16 + 4 * st + 2] = Kk[1];
+        rec[16 + 4 * st + 3] = Kk[2];
+      }
+    }
     const float b = (st == 0 || st == 3) ? (1.0f / 6.0f) : (1.0f / 3.0f);
     sk0 += b * Kk0;
     sk[0] += b * Kk[0];
@@ -552,6 +570,12 @@ __device__ bool ray_step_mixed(const DevField& F, const TraceArgsT& A, RayStateT
     offk[0] = c * Kk[0];
     offk[1] = c * Kk[1];
     offk[2] = c * Kk[2];
+  }
+  if constexpr (Record) {
+    if (rec) {
+      rec[32] = h;
+      rec[33] = last ? 1.0f : 0.0f;
+    }
   }
   const double hd = (double)h;
   bool finite = true;
