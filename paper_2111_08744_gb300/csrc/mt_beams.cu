@@ -81,7 +81,11 @@ __global__ void __launch_bounds__(kBeamBlock) beam_kernel(DevField F, DevCones C
   lc.key = (int4*)(smem + 16 * kBeamBlock) + threadIdx.x;
   lc.stride = kBeamBlock;
   lc.loc = (int4*)(smem + 16 * kBeamBlock) + kBeamBlock + threadIdx.x;
-  if (sizeof(T) == 4) *lc.loc = make_int4(0, 0, 0, -1);
+  lc.neg = (int4*)(smem + 16 * kBeamBlock) + 2 * kBeamBlock + threadIdx.x;
+  if (sizeof(T) == 4) {
+    *lc.loc = make_int4(0, 0, 0, -1);
+    lc.neg[0] = lc.neg[kBeamBlock] = make_int4(-1, 0, 0, 0);
+  }
   const LaneCache* lcp = sizeof(T) == 4 ? &lc : nullptr;
   RayState r;
   Beam b;
@@ -140,7 +144,7 @@ __global__ void __launch_bounds__(kBeamBlock) beam_kernel(DevField F, DevCones C
   }
 }
 
-constexpr size_t kBeamSmem = (size_t)kBeamBlock * (16 * sizeof(float4) + 2 * sizeof(int4));
+constexpr size_t kBeamSmem = (size_t)kBeamBlock * (16 * sizeof(float4) + 4 * sizeof(int4));
 
 template <class T, int IP>
 void launch_beams(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O, double* jac,

@@ -99,7 +99,11 @@ __global__ void __launch_bounds__(kLensBlock) lensing_kernel(DevField F, DevCone
   lc.key = (int4*)(smem + 16 * kLensBlock) + threadIdx.x;
   lc.stride = kLensBlock;
   lc.loc = (int4*)(smem + 16 * kLensBlock) + kLensBlock + threadIdx.x;
-  if (sizeof(T) == 4) *lc.loc = make_int4(0, 0, 0, -1);
+  lc.neg = (int4*)(smem + 16 * kLensBlock) + 2 * kLensBlock + threadIdx.x;
+  if (sizeof(T) == 4) {
+    *lc.loc = make_int4(0, 0, 0, -1);
+    lc.neg[0] = lc.neg[kLensBlock] = make_int4(-1, 0, 0, 0);
+  }
   const LaneCache* lcp = sizeof(T) == 4 ? &lc : nullptr;
   RayState r;
   InfBeam ib;
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(kLensBlock) lensing_kernel(DevField F, DevCone
   }
 }
 
-constexpr size_t kLensSmem = (size_t)kLensBlock * (16 * sizeof(float4) + 2 * sizeof(int4));
+constexpr size_t kLensSmem = (size_t)kLensBlock * (16 * sizeof(float4) + 4 * sizeof(int4));
 
 template <class T, int IP>
 void launch_lensing(const mt_octree* tree, const DevCones& C, const double* dirs, const OutPtrs& O, double* jac,

@@ -70,21 +70,22 @@ struct LaneCache {
   int4* loc;     // last locate answer: the cell (x, y, z) of level w that contains the point, w the
                  // finest level there (w = -1: empty); a property of the field, valid across rays;
                  // may be null
+  int4* neg = nullptr;  // neg[0], neg[stride]: keys (as `key`) of the lane's two last CIC (TSC)
+                        // neighbourhoods found incomplete at their level (level -1: empty); a property
+                        // of the field, valid across rays; may be null
 };
 
-// CIC at level l (FP32) from finest-level integer coordinates; v as in cic_gather.  With
-// WithD, dv[d][q] also receives the derivative of the interpolant of component q with respect
-// to the level-l cell coordinate d (the weights' derivatives, +-1 times the other two weights).
-// i0_out, f_out (if non-null) receive the lower corner and the in-cell fractions of the neighbourhood.
-template <bool WithD = false>
-__device__ __forceinline__ bool cic_int_cached(const DevField& F, int l, const int* ic, const float* fc, int s,
-                                               float* v, unsigned* err, const LaneCache& lc,
-                                               float (*dv)[8] = nullptr, int* i0_out = nullptr,
-                                               float* f_out = nullptr) {
+__device__ __forceinline__ bool same_key(const int4& a, const int4& b) {
+  return a.x == b.x && a.y == b.y && a.z == b.z && a.w == b.w;
+}
+
+// Lower corner and in-cell fractions of the level-l CIC neighbourhood of the point with
+// finest-level integer coordinates ic and fractions fc (Eq. 8: the 8 cells whose centres surround
+// it), and its key (level << 8 | slice, i0).
+__device__ __forceinline__ int4 cic_key(const DevField& F, int l, const int* ic, const float* fc, int s, int* i0,
+                                        float* f) {
   const int sh = F.L - l;
   const float inv = 1.0f / (float)(1 << sh);
-  int i0[3];
-  float f[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int ilev = ic[d] >> sh;
@@ -97,6 +98,50 @@ __device__ __forceinline__ bool cic_int_cached(const DevField& F, int l, const i
       f[d] = fl + 0.5f;
     }
   }
+  return make_int4((l << 8) | s, i0[0], i0[1], i0[2]);
+}
+
+// First level of the CIC fallback (Sect. 2.2, Fig. 1) for a point whose finest level is l: levels
+// whose neighbourhood of the point is one the lane found incomplete before are passed over
+// without probing (a neighbourhood's completeness is a property of the field), so a ray that
+// stays near the edge of a refined region does not re-probe the missing cells at every stage.
+__device__ __forceinline__ int cic_first_level(const DevField& F, int l, const int* ic, const float* fc, int s,
+                                               const LaneCache& lc) {
+  while (l > 0) {
+    int i0[3];
+    float f[3];
+    const int4 key = cic_key(F, l, ic, fc, s, i0, f);
+    if (!same_key(key, lc.neg[0]) && !same_key(key, lc.neg[lc.stride])) break;
+    --l;
+  }
+  return l;
+}
+
+// The same for TSC (Eq. 9): the neighbourhood of level l is the 27 cells around the point's
+// level-l cell, keyed by that cell (as tsc_gather_cached keys its rows).
+__device__ __forceinline__ int tsc_first_level(const DevField& F, int l, const int* ic, int s, const LaneCache& lc) {
+  while (l > 0) {
+    const int sh = F.L - l;
+    const int4 key = make_int4((l << 8) | s, ic[0] >> sh, ic[1] >> sh, ic[2] >> sh);
+    if (!same_key(key, lc.neg[0]) && !same_key(key, lc.neg[lc.stride])) break;
+    --l;
+  }
+  return l;
+}
+
+// CIC at level l (FP32) from finest-level integer coordinates; v as in cic_gather.  With
+// WithD, dv[d][q] also receives the derivative of the interpolant of component q with respect
+// to the level-l cell coordinate d (the weights' derivatives, +-1 times the other two weights).
+// i0_out, f_out (if non-null) receive the lower corner and the in-cell fractions of the neighbourhood.
+// A neighbourhood found incomplete (false) is remembered in lc.neg when the lane has one.
+template <bool WithD = false>
+__device__ __forceinline__ bool cic_int_cached(const DevField& F, int l, const int* ic, const float* fc, int s,
+                                               float* v, unsigned* err, const LaneCache& lc,
+                                               float (*dv)[8] = nullptr, int* i0_out = nullptr,
+                                               float* f_out = nullptr) {
+  int i0[3];
+  float f[3];
+  const int4 key = cic_key(F, l, ic, fc, s, i0, f);
   if (i0_out) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -104,9 +149,8 @@ __device__ __forceinline__ bool cic_int_cached(const DevField& F, int l, const i
       f_out[d] = f[d];
     }
   }
-  const int4 key = make_int4((l << 8) | s, i0[0], i0[1], i0[2]);
   const int4 old = *lc.key;
-  const bool hit = old.x == key.x && old.y == key.y && old.z == key.z && old.w == key.w;
+  const bool hit = same_key(old, key);
   // the miss path rejoins before the gather (no early exit from inside it): the lanes that staged a
   // new neighbourhood and those that reuse theirs then run the weights and the gather together
   bool ok = true;
@@ -125,6 +169,9 @@ __device__ __forceinline__ bool cic_int_cached(const DevField& F, int l, const i
         lc.rec[(2 * c + 1) * lc.stride] = __ldg(rc + s1);
       }
       *lc.key = key;
+    } else if (lc.neg) {
+      lc.neg[lc.stride] = lc.neg[0];
+      lc.neg[0] = key;
     }
   }
   if (!ok) return false;
@@ -203,7 +250,13 @@ __device__ __forceinline__ bool tsc_gather_cached(const DevField& F, int l, cons
   const int4 old = *lc.key;
   if (!(old.x == key.x && old.y == key.y && old.z == key.z && old.w == key.w)) {
     unsigned a[3][3], plo[3], oct[8];
-    if (!tsc_octets(F, l, c, a, plo, oct, err)) return false;
+    if (!tsc_octets(F, l, c, a, plo, oct, err)) {
+      if (lc.neg) {
+        lc.neg[lc.stride] = lc.neg[0];
+        lc.neg[0] = key;
+      }
+      return false;
+    }
 #pragma unroll 1
     for (int mz = 0; mz < 3; ++mz)
 #pragma unroll 1
@@ -397,12 +450,17 @@ __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const Mi
       float dv[WithD ? 3 : 1][8];
       int l = lfin;
       if constexpr (IP != MT_INTERP_CIC) {
+        if constexpr (IP == MT_INTERP_TSC) {
+          if (lc && lc->neg) l = tsc_first_level(F, l, ic, s, *lc);
+        }
         for (; l >= 0; --l)
           if (interp_int<WithD, IP>(F, l, ic, fc, s, v, err, WithD ? dv : nullptr, lc)) break;
       } else if constexpr (WithD) {
+        if (lc->neg) l = cic_first_level(F, l, ic, fc, s, *lc);
         for (; l >= 0; --l)
           if (cic_int_cached<true>(F, l, ic, fc, s, v, err, *lc, dv, sf->i0, sf->f)) break;
       } else if (lc) {
+        if (lc->neg) l = cic_first_level(F, l, ic, fc, s, *lc);
         for (; l >= 0; --l)
           if (cic_int_cached(F, l, ic, fc, s, v, err, *lc)) break;
       } else {

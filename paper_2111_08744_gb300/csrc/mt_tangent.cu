@@ -427,7 +427,9 @@ __global__ void __launch_bounds__(kTanBlock) tangent_kernel_mixed(DevField F, De
   lc.key = (int4*)(smem + 16 * kTanBlock) + threadIdx.x;
   lc.stride = kTanBlock;
   lc.loc = (int4*)(smem + 16 * kTanBlock) + kTanBlock + threadIdx.x;
+  lc.neg = (int4*)(smem + 16 * kTanBlock) + 2 * kTanBlock + threadIdx.x;
   *lc.loc = make_int4(0, 0, 0, -1);
+  lc.neg[0] = lc.neg[kTanBlock] = make_int4(-1, 0, 0, 0);
   RayState r;
   TanState ts;
   long long ray = -1;
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(kTanBlock) tangent_kernel_mixed(DevField F, De
   }
 }
 
-constexpr size_t kTanMixedSmem = (size_t)kTanBlock * (16 * sizeof(float4) + 2 * sizeof(int4));
+constexpr size_t kTanMixedSmem = (size_t)kTanBlock * (16 * sizeof(float4) + 4 * sizeof(int4));
 
 template <int IP>
 int tangent_mixed_blocks_per_sm() {
@@ -628,7 +630,11 @@ __global__ void __launch_bounds__(kTanBlock) finder_kernel(DevField F, DevCones 
   lc.key = (int4*)(smem + 16 * kTanBlock) + threadIdx.x;
   lc.stride = kTanBlock;
   lc.loc = (int4*)(smem + 16 * kTanBlock) + kTanBlock + threadIdx.x;
-  if (MIXED) *lc.loc = make_int4(0, 0, 0, -1);
+  lc.neg = (int4*)(smem + 16 * kTanBlock) + 2 * kTanBlock + threadIdx.x;
+  if (MIXED) {
+    *lc.loc = make_int4(0, 0, 0, -1);
+    lc.neg[0] = lc.neg[kTanBlock] = make_int4(-1, 0, 0, 0);
+  }
   const LaneCache* lcp = MIXED ? &lc : nullptr;
   long long src = -1;
   bool exhausted = false;

@@ -42,14 +42,18 @@ __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCone
   const unsigned lane = threadIdx.x & 31u;
   const long long n = A.n_rays;
   const bool grav = A.gravity_on != 0;
-  // mixed path: per-ray CIC neighbourhood staged in shared memory (16 float4 + key per thread)
+  // mixed path: per-ray CIC neighbourhood staged in shared memory (16 float4 + keys per thread)
   extern __shared__ float4 smem[];
   LaneCache lc;
   lc.rec = smem + threadIdx.x;
   lc.key = (int4*)(smem + 16 * BS) + threadIdx.x;
   lc.stride = BS;
   lc.loc = (int4*)(smem + 16 * BS) + BS + threadIdx.x;
-  if (sizeof(T) == 4 && Staged) *lc.loc = make_int4(0, 0, 0, -1);
+  lc.neg = (int4*)(smem + 16 * BS) + 2 * BS + threadIdx.x;
+  if (sizeof(T) == 4 && Staged) {
+    *lc.loc = make_int4(0, 0, 0, -1);
+    lc.neg[0] = lc.neg[BS] = make_int4(-1, 0, 0, 0);
+  }
   const LaneCache* lcp = (sizeof(T) == 4 && Staged) ? &lc : nullptr;
   const unsigned long long chunk = (unsigned long long)A.ray_chunk;
   RayState r;
@@ -101,10 +105,10 @@ __global__ void __launch_bounds__(BS, 512 / BS) trace_kernel(DevField F, DevCone
 }
 
 // Dynamic shared memory of trace_kernel<T, BS, IP, Staged>: the mixed path's per-thread neighbourhood
-// cache and last locate answer (288 B per thread).
+// cache, last locate answer and two incomplete-neighbourhood keys (320 B per thread).
 template <class T, int BS, bool Staged>
 constexpr size_t trace_smem() {
-  return (sizeof(T) == 4 && Staged) ? (size_t)BS * (16 * sizeof(float4) + 2 * sizeof(int4)) : 0;
+  return (sizeof(T) == 4 && Staged) ? (size_t)BS * (16 * sizeof(float4) + 4 * sizeof(int4)) : 0;
 }
 
 template <class T, int BS, int IP, bool Staged>
