@@ -52,11 +52,11 @@ FIELD_BYTES_BY_SCHEME = {"ngp": 4 * 1 * 16 * 2, "cic": FIELD_BYTES_PER_STEP, "ts
 TRACE_KERNEL_SOURCES = ["include/mt.h", "paper_2111_08744_gb300/csrc/mt_internal.cuh",
                         "paper_2111_08744_gb300/csrc/mt_mixed.cuh", "paper_2111_08744_gb300/csrc/mt_trace_device.cuh",
                         "paper_2111_08744_gb300/csrc/mt_trace.cu"]
-NCU_RECORD = {"sources_sha256": "55db78c4264d2c3ea744afeb9f4a1fad97f019a8b54eb53bf1b4b0a0614e1a85",
-              "dram_bytes_per_launch": 57933815552 + 966122752,
-              "per_rk4_step": {"warp_inst": 130.640, "fp64_lane_slots": 69.441},
-              "pct": {"fp64_pipe": 51.47, "issue_active": 48.72, "warps_active": 24.00, "lanes_per_inst": 15.66,
-                      "dram_throughput": 2.13, "l2_hit_rate": 49.25}}
+NCU_RECORD = {"sources_sha256": "21ab4e581ddbd8b74b17b9ed851c408b919a18b86015c87d00dea3d1743b33f5",
+              "dram_bytes_per_launch": 57904348416 + 992027136,
+              "per_rk4_step": {"warp_inst": 111.275, "fp64_lane_slots": 65.335},
+              "pct": {"fp64_pipe": 55.87, "issue_active": 47.83, "warps_active": 23.98, "lanes_per_inst": 19.18,
+                      "dram_throughput": 2.45, "l2_hit_rate": 47.85}}
 SMS, SCHEDULERS_PER_SM = 152, 4
 
 
