@@ -392,12 +392,11 @@ mt_status mt_field_from_coarse_phi(const mt_octree* tree, const double* phi0, co
  * are accepted; more return MT_ERR_UNSUPPORTED before any GPU work.
  *
  * The first call on a device looks up the static array's device address
- * (cudaGetSymbolAddress, once per device, with the octree's device current); make that
- * first call before any stream capture.  Every call clears the queue counter and rewrites
- * the cone table on `stream`, copying the table from pageable host memory, so the call
- * waits for earlier work on `stream` before it returns.  All calls share the one array:
- * calls that overlap on the GPU (other streams, other host threads) race and must be
- * serialised by the caller.  Device-side faults are flagged in the octree's status word
+ * (cudaGetSymbolAddress, once per device, with the octree's device current).  Every call
+ * clears the queue counter and rewrites the cone table on `stream`, copying the table from
+ * pageable host memory, so the call waits for earlier work on `stream` before it returns.
+ * All calls share the one array: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  Device-side faults are flagged in the octree's status word
  * (mt_device_status).
  */
 #define MT_NOALLOC_MAX_CONES 4096
