@@ -53,6 +53,9 @@ def test_roofline_arithmetic():
     assert abs(r["hbm_effective"]["achieved_GBs"] - 1024 * steps_per_s / 1e9) < 1e-6
     stale = bench.roofline(1e9, 500.0, 2000.0, 5e11, 6700.0, 1024, None, "test")
     assert stale["achieved"] is None and stale["traffic"] is None
+    assert stale["ncu_record"].startswith("stale")
+    other = bench.roofline(1e9, 500.0, 2000.0, 5e11, 6700.0, 1024, None, "test", "covers another workload")
+    assert other["ncu_record"] == "covers another workload" and other["frac"] is None
 
 
 def test_algorithmic_bytes_per_step():
