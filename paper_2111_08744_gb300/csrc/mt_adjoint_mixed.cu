@@ -75,7 +75,7 @@ __device__ void acc_add(const DevField& F, const RecBarM& R, const ScatterAcc& s
     acc_flush(F, R, sc);
     const long long i0l[3] = {sf.i0[0], sf.i0[1], sf.i0[2]};
     unsigned rows[8];
-    if (!cic_rows(F, sf.lev, i0l, rows, err)) return;  // the stage interpolated from these 8 cells
+    if (!cic_rows_compact(F, sf.lev, i0l, rows, err)) return;  // the stage interpolated from these 8 cells
 #pragma unroll
     for (int c = 0; c < 8; ++c) sc.rows[c * sc.stride] = rows[c];
     *sc.key = key;
@@ -98,7 +98,7 @@ __device__ void acc_add(const DevField& F, const RecBarM& R, const ScatterAcc& s
       a1[1 + i] = sf.wt * gbar[i];
     }
   }
-#pragma unroll
+#pragma unroll 1
   for (int c = 0; c < 8; ++c) {
     const float wx = (c & 1) ? sf.f[0] : 1.0f - sf.f[0];
     const float wy = (c & 2) ? sf.f[1] : 1.0f - sf.f[1];
@@ -220,7 +220,7 @@ __device__ bool reverse_step_mixed(const DevField& F, const TraceArgs& A, const 
     const float kv[3] = {ks[0] + okk(st, 1), ks[1] + okk(st, 2), ks[2] + okk(st, 3)};
     float Kk0, Kkv[3], KI, Ks;
     StageF sf;
-    if (!rhs_mixed<true, MT_INTERP_CIC>(F, Grav, B, eta, offx, offe, k0v, kv, &Kk0, Kkv, &KI, &Ks, nullptr, err,
+    if (!rhs_mixed<true, MT_INTERP_CIC, true>(F, Grav, B, eta, offx, offe, k0v, kv, &Kk0, Kkv, &KI, &Ks, nullptr, err,
                                         lc, &sf))
       return false;
     float gbar[3], pebar;
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(kAdjMBlock) count_mixed_kernel(DevField F, Dev
 // recompute records each step's stage data for the reverse step (rec null: no record).
 __device__ __noinline__ bool step_out_of_line(const DevField& F, const TraceArgs& A, RayState& r, unsigned* err,
                                               const LaneCache* lc, float* rec) {
-  return ray_step_mixed<MT_INTERP_CIC, true>(F, A, r, err, lc, rec);
+  return ray_step_mixed<MT_INTERP_CIC, true, true>(F, A, r, err, lc, rec);
 }
 
 // Scatter the cotangent phib of phi at the observer (the initial wave vector depends on it) onto the

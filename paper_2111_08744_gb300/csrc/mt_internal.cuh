@@ -253,6 +253,54 @@ __device__ __forceinline__ bool cic_rows(const DevField& F, int l, const long lo
   return true;
 }
 
+// The rows of cic_rows with the corner and octet loops kept rolled: the same lookups in about a
+// tenth of the instructions, out of line, for kernels whose hot loop outgrows the instruction
+// cache (one Morton key and one probe loop in the code instead of eight of each).
+static __device__ __noinline__ bool cic_rows_compact(const DevField& F, int l, const long long* i0, unsigned* rows,
+                                                     unsigned* err) {
+  const long long Nl = (long long)F.nc << l;
+  unsigned a0[3], a1[3];  // wrapped coordinates of the lower and upper corners per axis
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    long long v0 = i0[d], v1 = i0[d] + 1;
+    if (F.periodic) {
+      v0 &= (Nl - 1);
+      v1 &= (Nl - 1);
+    } else if (v0 < 0 || v1 >= Nl) {
+      return false;
+    }
+    a0[d] = (unsigned)v0;
+    a1[d] = (unsigned)v1;
+  }
+  if (l == 0) {
+#pragma unroll 1
+    for (int c = 0; c < 8; ++c)
+      rows[c] = (unsigned)morton((c & 1) ? a1[0] : a0[0], (c & 2) ? a1[1] : a0[1], (c & 4) ? a1[2] : a0[2]);
+    return true;
+  }
+  // parents of the two corners per axis coincide iff the lower corner index is even
+  const int ox = (int)(i0[0] & 1), oy = (int)(i0[1] & 1), oz = (int)(i0[2] & 1);
+  unsigned oct[8];
+#pragma unroll 1
+  for (int q = 0; q < 8; ++q) {
+    const int qx = q & 1, qy = (q >> 1) & 1, qz = (q >> 2) & 1;
+    if ((qx && !ox) || (qy && !oy) || (qz && !oz)) continue;
+    const unsigned long long pk = morton((qx ? a1[0] : a0[0]) >> 1, (qy ? a1[1] : a0[1]) >> 1, (qz ? a1[2] : a0[2]) >> 1);
+    const long long o = hash_find(F.hash[l], pk, err);
+    if (o < 0) return false;
+    oct[q] = (unsigned)o;
+  }
+#pragma unroll 1
+  for (int c = 0; c < 8; ++c) {
+    const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+    const int q = (ox ? cx : 0) | ((oy ? cy : 0) << 1) | ((oz ? cz : 0) << 2);
+    const unsigned child = ((cx ? a1[0] : a0[0]) & 1u) | (((cy ? a1[1] : a0[1]) & 1u) << 1) |
+                           (((cz ? a1[2] : a0[2]) & 1u) << 2);
+    rows[c] = oct[q] * 8u + child;
+  }
+  return true;
+}
+
 // CIC (Eq. 8) gather at level l around lower corner i0, for the two bracketing slices s, s+1 (or
 // slice 0 when S = 1): out[0..3] at slice s, out[4..7] at slice s+1.  w[d][b]: the weight along axis
 // d of the corner i0_d + b; corner c weighs w[0][c & 1] w[1][c >> 1 & 1] w[2][c >> 2 & 1].  Returns

@@ -134,7 +134,9 @@ __device__ __forceinline__ int tsc_first_level(const DevField& F, int l, const i
 // to the level-l cell coordinate d (the weights' derivatives, +-1 times the other two weights).
 // i0_out, f_out (if non-null) receive the lower corner and the in-cell fractions of the neighbourhood.
 // A neighbourhood found incomplete (false) is remembered in lc.neg when the lane has one.
-template <bool WithD = false>
+// Compact: the miss path looks the rows up out of line and the corner loop stays rolled (the same
+// arithmetic in fewer instructions, for kernels whose hot loop outgrows the instruction cache).
+template <bool WithD = false, bool Compact = false>
 __device__ __forceinline__ bool cic_int_cached(const DevField& F, int l, const int* ic, const float* fc, int s,
                                                float* v, unsigned* err, const LaneCache& lc,
                                                float (*dv)[8] = nullptr, int* i0_out = nullptr,
@@ -157,7 +159,11 @@ __device__ __forceinline__ bool cic_int_cached(const DevField& F, int l, const i
   if (!hit) {
     const long long i0l[3] = {i0[0], i0[1], i0[2]};
     unsigned rows[8];
-    ok = cic_rows(F, l, i0l, rows, err);
+    if constexpr (Compact) {
+      ok = cic_rows_compact(F, l, i0l, rows, err);
+    } else {
+      ok = cic_rows(F, l, i0l, rows, err);
+    }
     if (ok) {
       const float4* rec = (const float4*)F.rec[l];
       const int S = F.S;
@@ -181,7 +187,7 @@ __device__ __forceinline__ bool cic_int_cached(const DevField& F, int l, const i
 #pragma unroll
     for (int q = 0; q < 8; ++q) dv[0][q] = dv[1][q] = dv[2][q] = 0.0f;
   }
-#pragma unroll
+#pragma unroll(Compact ? 1 : 8)
   for (int c = 0; c < 8; ++c) {
     const float wx = (c & 1) ? f[0] : 1.0f - f[0];
     const float wy = (c & 2) ? f[1] : 1.0f - f[1];
@@ -393,7 +399,7 @@ struct StageF {
 // FP32 right-hand side of Eqs. (2)-(4) at the stage with offsets (offx, offe) from the step
 // start and wave vector (k0, k).  *lf (if non-null) receives the most refined level.  With
 // WithD (which needs the lane cache) *sf receives the stage's field values and derivatives.
-template <bool WithD = false, int IP = MT_INTERP_CIC>
+template <bool WithD = false, int IP = MT_INTERP_CIC, bool Compact = false>
 __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const MixedStep& B, double eta_step,
                                           const float* offx, float offe, float k0, const float* k, float* Kk0,
                                           float* Kk, float* KI, float* Ks, int* lf, unsigned* err,
@@ -458,11 +464,11 @@ __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const Mi
       } else if constexpr (WithD) {
         if (lc->neg) l = cic_first_level(F, l, ic, fc, s, *lc);
         for (; l >= 0; --l)
-          if (cic_int_cached<true>(F, l, ic, fc, s, v, err, *lc, dv, sf->i0, sf->f)) break;
+          if (cic_int_cached<true, Compact>(F, l, ic, fc, s, v, err, *lc, dv, sf->i0, sf->f)) break;
       } else if (lc) {
         if (lc->neg) l = cic_first_level(F, l, ic, fc, s, *lc);
         for (; l >= 0; --l)
-          if (cic_int_cached(F, l, ic, fc, s, v, err, *lc)) break;
+          if (cic_int_cached<false, Compact>(F, l, ic, fc, s, v, err, *lc)) break;
       } else {
         for (; l >= 0; --l)
           if (cic_int(F, l, ic, fc, s, v, err)) break;
@@ -553,8 +559,9 @@ __device__ __forceinline__ bool mixed_begin(const DevField& F, const double* y, 
 constexpr int kStepRecordFloats = 34;  // [0, 16) offsets, [16, 32) right-hand sides, 32: h, 33: last
 
 // One mixed-precision RK4 step; state and status conventions as ray_step.  Record: if rec is not
-// null it receives the step's stage data (kStepRecordFloats floats).
-template <int IP = MT_INTERP_CIC, bool Record = false, class RayStateT, class TraceArgsT>
+// null it receives the step's stage data (kStepRecordFloats floats).  Compact: the CIC in the
+// compact form of cic_int_cached (same results).
+template <int IP = MT_INTERP_CIC, bool Record = false, bool Compact = false, class RayStateT, class TraceArgsT>
 __device__ bool ray_step_mixed(const DevField& F, const TraceArgsT& A, RayStateT& r, unsigned* err,
                                const LaneCache* lc = nullptr, float* rec = nullptr) {
   if (r.n_steps == 0 && !(r.y[3] > r.eta_stop)) return true;
@@ -582,7 +589,7 @@ __device__ bool ray_step_mixed(const DevField& F, const TraceArgsT& A, RayStateT
     const float kst[3] = {ks[0] + offk[0], ks[1] + offk[1], ks[2] + offk[2]};
     float Kk0, Kk[3], KI, Ks;
     int lf = 0;
-    if (!rhs_mixed<false, IP>(F, grav, B, eta, offx, offe, kst0, kst, &Kk0, Kk, &KI, &Ks, st == 0 ? &lf : nullptr, err,
+    if (!rhs_mixed<false, IP, Compact>(F, grav, B, eta, offx, offe, kst0, kst, &Kk0, Kk, &KI, &Ks, st == 0 ? &lf : nullptr, err,
                               lc)) {
       r.status = MT_RAY_LEFT_DOMAIN;
       return true;
