@@ -3,10 +3,13 @@
 // loss on the end points with respect to the records (Sect. 2.2: RK4 of Eqs. 2-4, CIC with level
 // fallback, slices linear in eta).
 //
-// Per ray (one lane; a warp takes 32 consecutive ray ids at a time and runs their phases in lockstep):
-//   1. integrate forward with the mixed step, keeping the FP64 state every `checkpoint_every` steps;
+// Per ray:
+//   1. integrate forward with the mixed step (checkpoint_mixed_kernel, scheduled as trace_kernel:
+//      a lane whose ray ends takes the next id of its warp's chunk), keeping the FP64 state every
+//      `checkpoint_every` steps, and write the ray's outputs;
 //   2. form the cotangent of the final state from dL/dxi, xi = x - (k/k0)(eta - eta_stop);
-//   3. for each segment, last to first: recompute its steps from the checkpoint, keeping each step's
+//   3. (adjoint_mixed_kernel: a warp takes 32 consecutive ray ids at a time and runs their phases in
+//      lockstep) for each segment, last to first: recompute its steps from the checkpoint, keeping each step's
 //      start state and stage data (the stage wave-vector offsets, right-hand sides and step size),
 //      then reverse each step: the stages from the last to the first are evaluated again with the
 //      derivatives of the CIC interpolant (FP32) and their transposed Jacobians applied in FP32 to
@@ -324,6 +327,86 @@ __global__ void __launch_bounds__(kAdjMBlock) count_mixed_kernel(DevField F, Dev
   }
 }
 
+// Forward pass of the reverse mode, with the scheduling of trace_kernel (a lane whose ray ends takes
+// the next id of its warp's chunk): the mixed trace of every ray, writing its FP64 state every seg_len
+// steps into its checkpoint slots (ck_off), its outputs, and what the sweep starts from: the cotangent
+// of the end state from dL/dxi (xi = x - (k/k0)(eta - eta_stop)) in yb0[0..7][n], phi at the observer
+// in yb0[8][n], and the number of steps to reverse in n_rev (0 for a ray that did not end with
+// MT_RAY_OK).
+__global__ void __launch_bounds__(kAdjMBlock, 4) checkpoint_mixed_kernel(DevField F, DevCones C,
+                                                                      const double* __restrict__ dirs, OutPtrs O,
+                                                                      TraceArgs A, const double* __restrict__ dL_dxi,
+                                                                      double* ckpt, const long long* ck_off, int seg_len,
+                                                                      double* yb0, int* n_rev, unsigned long long* ws) {
+  unsigned* err = (unsigned*)(ws + 1);
+  extern __shared__ float4 smem_k[];
+  LaneCache lc;
+  lane_cache_init(lc, smem_k);
+  const unsigned lane = threadIdx.x & 31u;
+  const long long n = A.n_rays;
+  const bool grav = A.gravity_on != 0;
+  WarpQueue q;
+  long long ray = -1;
+  bool exhausted = false;
+  RayState r;
+  long long off = 0, n_ck = 0;
+  bool ok = false;
+  for (;;) {
+    const bool need = ray < 0 && !exhausted;
+    const long long id = q.next(need, lane, ws);
+    if (need) {
+      if (id >= 0 && id < n) {
+        ray = id;
+        int c = 0;
+        while (c + 1 < C.n && C.begin[c + 1] <= ray) ++c;
+        r = ray_start<float>(F, C.obs[c], C.eta_stop[c], dirs, n, ray, grav, err);
+        off = ck_off[ray];
+        n_ck = ck_off[ray + 1] - off;
+        ok = true;
+        *lc.key = make_int4(-1, 0, 0, 0);
+      } else {
+        exhausted = true;
+      }
+    }
+    if (!__any_sync(0xffffffffu, ray >= 0)) break;
+    if (ray < 0) continue;
+    bool done = false;
+    if (r.n_steps % seg_len == 0) {
+      const long long j = r.n_steps / seg_len;
+      if (j >= n_ck) {
+        atomicOr(err, kErrOOB);  // more steps than the counting pass found
+        ok = false;
+        done = true;
+      } else {
+        double* cp = ckpt + (off + j) * 8;
+        for (int i = 0; i < 8; ++i) cp[i] = r.y[i];
+      }
+    }
+    if (!done) done = ray_step_mixed<MT_INTERP_CIC>(F, A, r, err, &lc);
+    if (done) {
+      ray_finish<float>(F, A, r, ray, n, O, err);
+      const bool active = ok && r.status == MT_RAY_OK && r.n_steps > 0;
+      double yb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (active) {
+        const double* y = r.y;
+        const double k0 = y[4], de = y[3] - r.eta_stop;
+        const double xb[3] = {dL_dxi[ray], dL_dxi[n + ray], dL_dxi[2 * n + ray]};
+        const double xk = xb[0] * y[5] + xb[1] * y[6] + xb[2] * y[7];
+        for (int d = 0; d < 3; ++d) {
+          yb[d] = xb[d];
+          yb[5 + d] = -xb[d] * de / k0;
+        }
+        yb[3] = -xk / k0;
+        yb[4] = xk * de / (k0 * k0);
+      }
+      for (int i = 0; i < 8; ++i) yb0[i * n + ray] = yb[i];
+      yb0[8 * n + ray] = r.phi_o;
+      n_rev[ray] = active ? r.n_steps : 0;
+      ray = -1;
+    }
+  }
+}
+
 // The mixed step, out of line: the forward pass and the segment recompute of the reverse sweep share
 // one copy of its code (inlined copies beside the reverse step outgrow the instruction cache); the
 // recompute records each step's stage data for the reverse step (rec null: no record).
@@ -372,16 +455,20 @@ __device__ void scatter_observer(const DevField& F, const RecBarM& R, const doub
   }
 }
 
-// Warp-synchronous sweep: a warp takes 32 consecutive rays per turn (sky neighbours), integrates
-// them forward together (lanes whose ray has ended wait), then reverses them segment by segment,
-// aligned on each ray's last segment, with warp-uniform loop bounds, so that the lanes run the same
-// phase (recompute or reverse) at the same time; only the rays' different step counts leave lanes idle.
+// Warp-synchronous sweep: a warp takes 32 consecutive rays per turn (sky neighbours), starts from
+// what checkpoint_mixed_kernel left (step counts, checkpoints, end cotangents, phi at the observer)
+// and reverses them segment by segment, aligned on each ray's last segment, with warp-uniform loop
+// bounds, so that the lanes run the same phase (recompute or reverse) at the same time; only the
+// rays' different step counts leave lanes idle.  The segment recompute evaluates the forward pass's
+// arithmetic (the mixed step, its CIC in the compact form, which changes no result), so it retraces
+// the forward pass bit for bit.
 template <bool Grav>
 __global__ void __launch_bounds__(kAdjMBlock, 3) adjoint_mixed_kernel(DevField F, DevCones C,
-                                                                   const double* __restrict__ dirs, OutPtrs O,
-                                                                   TraceArgs A, const double* __restrict__ dL_dxi,
-                                                                   RecBarM R, double* ckpt, const long long* ck_off,
-                                                                   int seg_len, unsigned long long* ws) {
+                                                                   const double* __restrict__ dirs, TraceArgs A,
+                                                                   RecBarM R, const double* ckpt,
+                                                                   const long long* ck_off, int seg_len,
+                                                                   const double* yb0, const int* n_rev,
+                                                                   unsigned long long* ws) {
   unsigned* err = (unsigned*)(ws + 1);
   extern __shared__ float4 smem_a[];
   LaneCache lc;
@@ -405,54 +492,30 @@ __global__ void __launch_bounds__(kAdjMBlock, 3) adjoint_mixed_kernel(DevField F
     if (base >= (unsigned long long)n) break;
     const long long ray = (long long)base + lane;
     const bool have = ray < n;
+    // the ray's forward pass (checkpoint_mixed_kernel): its step count, checkpoints and end cotangent
     RayState r;
-    long long off = 0, n_ck = 0;
-    bool ok = have;
+    long long off = 0;
+    int n_steps = 0;
+    double yb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (have) {
       int c = 0;
       while (c + 1 < C.n && C.begin[c + 1] <= ray) ++c;
-      r = ray_start<float>(F, C.obs[c], C.eta_stop[c], dirs, n, ray, Grav, err);
+      r.xo[0] = C.obs[c][0];
+      r.xo[1] = C.obs[c][1];
+      r.xo[2] = C.obs[c][2];
+      r.eta_stop = C.eta_stop[c];
+      r.y[8] = r.y[9] = 0.0;
+      r.lambda = 0.0;
+      r.phi_o = yb0[8 * n + ray];
+      r.status = MT_RAY_OK;
+      n_steps = n_rev[ray];
       off = ck_off[ray];
-      n_ck = ck_off[ray + 1] - off;
+      for (int i = 0; i < 8; ++i) yb[i] = yb0[i * n + ray];
     }
     *lc.key = make_int4(-1, 0, 0, 0);
-    // 1. forward with checkpoints, the warp's rays in lockstep
-    bool fwd = have;
-    while (__any_sync(0xffffffffu, fwd)) {
-      if (fwd) {
-        if (r.n_steps % seg_len == 0) {
-          const long long j = r.n_steps / seg_len;
-          if (j >= n_ck) {
-            atomicOr(err, kErrOOB);  // more steps than the counting pass found
-            ok = false;
-            fwd = false;
-          } else {
-            double* cp = ckpt + (off + j) * 8;
-            for (int i = 0; i < 8; ++i) cp[i] = r.y[i];
-          }
-        }
-        if (fwd && step_out_of_line(F, A, r, err, &lc, nullptr)) fwd = false;
-      }
-    }
-    if (have) ray_finish<float>(F, A, r, ray, n, O, err);
-    const bool active = ok && have && r.status == MT_RAY_OK && r.n_steps > 0;
-    const int n_steps = active ? r.n_steps : 0;
+    const bool active = n_steps > 0;
     const int n_seg = (n_steps + seg_len - 1) / seg_len;
     const int max_seg = (int)__reduce_max_sync(0xffffffffu, (unsigned)n_seg);
-    // 2. cotangent of the end state from dL/dxi
-    double yb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (active) {
-      const double* y = r.y;
-      const double k0 = y[4], de = y[3] - r.eta_stop;
-      const double xb[3] = {dL_dxi[ray], dL_dxi[n + ray], dL_dxi[2 * n + ray]};
-      const double xk = xb[0] * y[5] + xb[1] * y[6] + xb[2] * y[7];
-      for (int d = 0; d < 3; ++d) {
-        yb[d] = xb[d];
-        yb[5 + d] = -xb[d] * de / k0;
-      }
-      yb[3] = -xk / k0;
-      yb[4] = xk * de / (k0 * k0);
-    }
     // 3. segments from the last, aligned on each ray's last segment
     bool alive = active;
     for (int j = max_seg - 1; j >= 0; --j) {
@@ -509,6 +572,7 @@ mt_status run_adjoint_mixed(const mt_octree* tree, const DevCones& C, const doub
   int* d_steps = nullptr;
   long long* d_off = nullptr;
   double* d_ck = nullptr;
+  double* d_yb0 = nullptr;
   cudaError_t e = cudaMalloc(&d_steps, sizeof(int) * std::max<long long>(1, n));
   if (e == cudaSuccess) e = cudaMemsetAsync(tree->ws, 0, sizeof(unsigned long long), stream);
   if (e == cudaSuccess) {
@@ -526,6 +590,24 @@ mt_status run_adjoint_mixed(const mt_octree* tree, const DevCones& C, const doub
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = adjoint_checkpoint_layout(d_steps, n, checkpoint_every, &d_off, &d_ck, stream);
+  // forward pass: checkpoints, outputs and the end cotangents
+  if (e == cudaSuccess) e = cudaMalloc(&d_yb0, sizeof(double) * 9 * (size_t)std::max<long long>(1, n));
+  if (e == cudaSuccess) e = cudaMemsetAsync(tree->ws, 0, sizeof(unsigned long long), stream);
+  if (e == cudaSuccess) {
+    static int bps_k = -1;
+    if (bps_k < 0) {
+      int b = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, checkpoint_mixed_kernel, kAdjMBlock, kLaneCacheBytes) !=
+              cudaSuccess ||
+          b < 1)
+        b = 1;
+      bps_k = b;
+    }
+    checkpoint_mixed_kernel<<<tree->num_sms * bps_k, kAdjMBlock, kLaneCacheBytes, stream>>>(
+        launch_field(tree, A), C, dirs, O, A, dL_dxi, d_ck, d_off, checkpoint_every, d_yb0, d_steps, tree->ws);
+    e = cudaGetLastError();
+  }
+  // reverse sweep
   if (e == cudaSuccess) e = cudaMemsetAsync(tree->ws, 0, sizeof(unsigned long long), stream);
   if (e == cudaSuccess) {
     const size_t smem = kLaneCacheBytes + kAccBytes;
@@ -538,12 +620,13 @@ mt_status run_adjoint_mixed(const mt_octree* tree, const DevCones& C, const doub
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kAdjMBlock, smem) != cudaSuccess || b < 1) b = 1;
       bps[g] = b;
     }
+    const int grid = tree->num_sms * bps[g];
     if (g) {
-      adjoint_mixed_kernel<true><<<tree->num_sms * bps[g], kAdjMBlock, smem, stream>>>(
-          launch_field(tree, A), C, dirs, O, A, dL_dxi, R, d_ck, d_off, checkpoint_every, tree->ws);
+      adjoint_mixed_kernel<true><<<grid, kAdjMBlock, smem, stream>>>(launch_field(tree, A), C, dirs, A, R, d_ck, d_off,
+                                                                     checkpoint_every, d_yb0, d_steps, tree->ws);
     } else {
-      adjoint_mixed_kernel<false><<<tree->num_sms * bps[g], kAdjMBlock, smem, stream>>>(
-          launch_field(tree, A), C, dirs, O, A, dL_dxi, R, d_ck, d_off, checkpoint_every, tree->ws);
+      adjoint_mixed_kernel<false><<<grid, kAdjMBlock, smem, stream>>>(launch_field(tree, A), C, dirs, A, R, d_ck, d_off,
+                                                                      checkpoint_every, d_yb0, d_steps, tree->ws);
     }
     e = cudaGetLastError();
   }
@@ -551,6 +634,7 @@ mt_status run_adjoint_mixed(const mt_octree* tree, const DevCones& C, const doub
   if (d_steps) cudaFree(d_steps);
   if (d_off) cudaFree(d_off);
   if (d_ck) cudaFree(d_ck);
+  if (d_yb0) cudaFree(d_yb0);
   if (e == cudaErrorMemoryAllocation) return MT_ERR_OOM;
   return (e == cudaSuccess && e2 == cudaSuccess) ? MT_OK : MT_ERR_CUDA;
 }

@@ -287,6 +287,27 @@ def test_mixed_reverse_checkpoint_interval_does_not_change_gradients():
         np.testing.assert_allclose(x, y, rtol=1e-9, atol=1e-9 * np.abs(x).max())
 
 
+@pytest.mark.parametrize("which", ["small", "diff_patch"])
+def test_mixed_reverse_traces_the_same_map_as_the_forward_trace(which):
+    """FP32 octree: the reverse mode differentiates the map mt_trace_rays computes, so the rays its
+    forward pass and segment recomputes integrate are the trace's, bit for bit: every end-point
+    output of mt_trace_rays_adjoint (record gradients requested) equals mt_trace_rays's."""
+    import torch
+    from paper_2111_08744_gb300 import binding as B
+    w = _small() if which == "small" else _diff_patch()
+    tree = B.Octree(w.box, w.n_coarse, w.periodic, w.slice_eta, I.fp32_levels(w), w.bg, "fp32")
+    params = B.TraceParams.from_workload(w)
+    dirs = torch.from_numpy(w.dirs).cuda()
+    ref = B.trace_rays(tree, params, dirs)
+    wxi = torch.from_numpy(np.random.Generator(np.random.PCG64(34)).normal(size=(3, w.n_rays))).cuda()
+    got = B.trace_rays_adjoint(tree, params, dirs, jacobian=False, lensing=False, dL_dxi=wxi, checkpoint_every=16)
+    torch.cuda.synchronize()
+    assert tree.device_status() == B.MT_OK
+    tree.free()
+    for k in B.OUT_F64 + B.OUT_I32 + ["xi"]:
+        assert torch.equal(got[k], ref[k]), k
+
+
 def test_field_model_forward_on_the_gpu_matches_the_generator():
     """mt_field_from_coarse_phi (phi_0 -> records of every level) against the generator's field model
     (inputs.records_from_phi0) for a random phi_0, element by element; it is the transpose of the
