@@ -288,7 +288,16 @@ __device__ void lane_cache_init(LaneCache& lc, float4* smem) {
   *lc.key = make_int4(-1, 0, 0, 0);
 }
 
+// The same with the keys of the lane's last two incomplete CIC neighbourhoods (the level fallback
+// passes over them without probing, as in trace_kernel), for the forward kernels.
+__device__ void lane_cache_init_neg(LaneCache& lc, float4* smem) {
+  lane_cache_init(lc, smem);
+  lc.neg = (int4*)(smem + 16 * kAdjMBlock) + 2 * kAdjMBlock + threadIdx.x;
+  lc.neg[0] = lc.neg[kAdjMBlock] = make_int4(-1, 0, 0, 0);
+}
+
 constexpr size_t kLaneCacheBytes = (size_t)kAdjMBlock * (16 * sizeof(float4) + 2 * sizeof(int4));
+constexpr size_t kLaneCacheNegBytes = kLaneCacheBytes + (size_t)kAdjMBlock * 2 * sizeof(int4);
 constexpr size_t kAccBytes = (size_t)kAdjMBlock * (64 * sizeof(float) + 8 * sizeof(unsigned) + sizeof(int4));
 
 // Step counts of the mixed trace (the checkpoint layout).
@@ -297,7 +306,7 @@ __global__ void __launch_bounds__(kAdjMBlock) count_mixed_kernel(DevField F, Dev
   unsigned* err = (unsigned*)(ws + 1);
   extern __shared__ float4 smem_c[];
   LaneCache lc;
-  lane_cache_init(lc, smem_c);
+  lane_cache_init_neg(lc, smem_c);
   const unsigned lane = threadIdx.x & 31u;
   const long long n = A.n_rays;
   const bool grav = A.gravity_on != 0;
@@ -341,7 +350,7 @@ __global__ void __launch_bounds__(kAdjMBlock, 4) checkpoint_mixed_kernel(DevFiel
   unsigned* err = (unsigned*)(ws + 1);
   extern __shared__ float4 smem_k[];
   LaneCache lc;
-  lane_cache_init(lc, smem_k);
+  lane_cache_init_neg(lc, smem_k);
   const unsigned lane = threadIdx.x & 31u;
   const long long n = A.n_rays;
   const bool grav = A.gravity_on != 0;
@@ -410,7 +419,7 @@ __global__ void __launch_bounds__(kAdjMBlock, 4) checkpoint_mixed_kernel(DevFiel
 // The mixed step, out of line: the forward pass and the segment recompute of the reverse sweep share
 // one copy of its code (inlined copies beside the reverse step outgrow the instruction cache); the
 // recompute records each step's stage data for the reverse step (rec null: no record).
-__device__ __noinline__ bool step_out_of_line(const DevField& F, const TraceArgs& A, RayState& r, unsigned* err,
+__device__ __forceinline__ bool step_out_of_line(const DevField& F, const TraceArgs& A, RayState& r, unsigned* err,
                                               const LaneCache* lc, float* rec) {
   return ray_step_mixed<MT_INTERP_CIC, true, true>(F, A, r, err, lc, rec);
 }
@@ -579,14 +588,14 @@ mt_status run_adjoint_mixed(const mt_octree* tree, const DevCones& C, const doub
     static int bps_c = -1;
     if (bps_c < 0) {
       int b = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, count_mixed_kernel, kAdjMBlock, kLaneCacheBytes) !=
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, count_mixed_kernel, kAdjMBlock, kLaneCacheNegBytes) !=
               cudaSuccess ||
           b < 1)
         b = 1;
       bps_c = b;
     }
-    count_mixed_kernel<<<tree->num_sms * bps_c, kAdjMBlock, kLaneCacheBytes, stream>>>(launch_field(tree, A), C,
-                                                                                         dirs, A, d_steps, tree->ws);
+    count_mixed_kernel<<<tree->num_sms * bps_c, kAdjMBlock, kLaneCacheNegBytes, stream>>>(launch_field(tree, A), C,
+                                                                                            dirs, A, d_steps, tree->ws);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = adjoint_checkpoint_layout(d_steps, n, checkpoint_every, &d_off, &d_ck, stream);
@@ -597,13 +606,13 @@ mt_status run_adjoint_mixed(const mt_octree* tree, const DevCones& C, const doub
     static int bps_k = -1;
     if (bps_k < 0) {
       int b = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, checkpoint_mixed_kernel, kAdjMBlock, kLaneCacheBytes) !=
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, checkpoint_mixed_kernel, kAdjMBlock, kLaneCacheNegBytes) !=
               cudaSuccess ||
           b < 1)
         b = 1;
       bps_k = b;
     }
-    checkpoint_mixed_kernel<<<tree->num_sms * bps_k, kAdjMBlock, kLaneCacheBytes, stream>>>(
+    checkpoint_mixed_kernel<<<tree->num_sms * bps_k, kAdjMBlock, kLaneCacheNegBytes, stream>>>(
         launch_field(tree, A), C, dirs, O, A, dL_dxi, d_ck, d_off, checkpoint_every, d_yb0, d_steps, tree->ws);
     e = cudaGetLastError();
   }
