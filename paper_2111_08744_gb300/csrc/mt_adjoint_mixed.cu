@@ -76,11 +76,16 @@ __device__ void acc_add(const DevField& F, const RecBarM& R, const ScatterAcc& s
   const int4 old = *sc.key;
   if (!(old.x == key.x && old.y == key.y && old.z == key.z && old.w == key.w)) {
     acc_flush(F, R, sc);
-    const long long i0l[3] = {sf.i0[0], sf.i0[1], sf.i0[2]};
-    unsigned rows[8];
-    if (!cic_rows_compact(F, sf.lev, i0l, rows, err)) return;  // the stage interpolated from these 8 cells
+    if (sf.rows_ok) {  // the stage staged this neighbourhood and looked its rows up already
 #pragma unroll
-    for (int c = 0; c < 8; ++c) sc.rows[c * sc.stride] = rows[c];
+      for (int c = 0; c < 8; ++c) sc.rows[c * sc.stride] = sf.rows[c];
+    } else {
+      const long long i0l[3] = {sf.i0[0], sf.i0[1], sf.i0[2]};
+      unsigned rows[8];
+      if (!cic_rows_compact(F, sf.lev, i0l, rows, err)) return;  // the stage interpolated from these 8 cells
+#pragma unroll
+      for (int c = 0; c < 8; ++c) sc.rows[c * sc.stride] = rows[c];
+    }
     *sc.key = key;
   }
   float a0[4], a1[4];

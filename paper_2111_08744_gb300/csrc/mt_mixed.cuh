@@ -140,7 +140,8 @@ template <bool WithD = false, bool Compact = false>
 __device__ __forceinline__ bool cic_int_cached(const DevField& F, int l, const int* ic, const float* fc, int s,
                                                float* v, unsigned* err, const LaneCache& lc,
                                                float (*dv)[8] = nullptr, int* i0_out = nullptr,
-                                               float* f_out = nullptr) {
+                                               float* f_out = nullptr, unsigned* rows_out = nullptr,
+                                               bool* rows_ok = nullptr) {
   int i0[3];
   float f[3];
   const int4 key = cic_key(F, l, ic, fc, s, i0, f);
@@ -175,6 +176,11 @@ __device__ __forceinline__ bool cic_int_cached(const DevField& F, int l, const i
         lc.rec[(2 * c + 1) * lc.stride] = __ldg(rc + s1);
       }
       *lc.key = key;
+      if (rows_out) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) rows_out[c] = rows[c];
+        *rows_ok = true;
+      }
     } else if (lc.neg) {
       lc.neg[lc.stride] = lc.neg[0];
       lc.neg[0] = key;
@@ -394,6 +400,9 @@ struct StageF {
   int i0[3];
   float f[3];
   float wt, ids;
+  // the rows of the 8 cells, when the stage staged the neighbourhood (rows_ok; CIC only)
+  unsigned rows[8];
+  bool rows_ok;
 };
 
 // FP32 right-hand side of Eqs. (2)-(4) at the stage with offsets (offx, offe) from the step
@@ -463,8 +472,11 @@ __device__ __forceinline__ bool rhs_mixed(const DevField& F, bool grav, const Mi
           if (interp_int<WithD, IP>(F, l, ic, fc, s, v, err, WithD ? dv : nullptr, lc)) break;
       } else if constexpr (WithD) {
         if (lc->neg) l = cic_first_level(F, l, ic, fc, s, *lc);
+        sf->rows_ok = false;
         for (; l >= 0; --l)
-          if (cic_int_cached<true, Compact>(F, l, ic, fc, s, v, err, *lc, dv, sf->i0, sf->f)) break;
+          if (cic_int_cached<true, Compact>(F, l, ic, fc, s, v, err, *lc, dv, sf->i0, sf->f, sf->rows,
+                                            &sf->rows_ok))
+            break;
       } else if (lc) {
         if (lc->neg) l = cic_first_level(F, l, ic, fc, s, *lc);
         for (; l >= 0; --l)
