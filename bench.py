@@ -45,18 +45,16 @@ FIELD_BYTES_BY_SCHEME = {"ngp": 4 * 1 * 16 * 2, "cic": FIELD_BYTES_PER_STEP, "ts
 #       occupied per step = sm__pipe_fp64_cycles_active.sum x 2 lanes per cycle (the pipe's peak, 2
 #       DFMA lanes per cycle per SM; a warp instruction holds it 16 cycles) / steps;
 #   pct: fp64_pipe = sm__pipe_fp64_cycles_active.sum / sm__cycles_active.sum; issue_active =
-#       smsp__issue_active.sum / (4 x sm__cycles_active.sum); warps_active = sm__warps_active.sum /
-#       (64 x sm__cycles_active.sum); lanes_per_inst = smsp__thread_inst_executed.sum /
-#       smsp__inst_executed.sum; dram_throughput = the DRAM bytes over the launch time against the
-#       measured copy rate; l2_hit_rate from the --set full capture of a 65,536-ray launch.
+#       smsp__inst_executed.sum / (4 x sm__cycles_active.sum) (instructions per scheduler cycle);
+#       lanes_per_inst = smsp__thread_inst_executed.sum / smsp__inst_executed.sum; dram_throughput =
+#       the DRAM bytes over the launch time against the measured copy rate.
 TRACE_KERNEL_SOURCES = ["include/mt.h", "paper_2111_08744_gb300/csrc/mt_internal.cuh",
                         "paper_2111_08744_gb300/csrc/mt_mixed.cuh", "paper_2111_08744_gb300/csrc/mt_trace_device.cuh",
                         "paper_2111_08744_gb300/csrc/mt_trace.cu"]
-NCU_RECORD = {"sources_sha256": "21ab4e581ddbd8b74b17b9ed851c408b919a18b86015c87d00dea3d1743b33f5",
-              "dram_bytes_per_launch": 57904348416 + 992027136,
-              "per_rk4_step": {"warp_inst": 111.275, "fp64_lane_slots": 65.335},
-              "pct": {"fp64_pipe": 55.87, "issue_active": 47.83, "warps_active": 23.98, "lanes_per_inst": 19.18,
-                      "dram_throughput": 2.45, "l2_hit_rate": 47.85}}
+NCU_RECORD = {"sources_sha256": "2368f9aab23d743202379115c02b85402050b066535b7419fec988e027c320c6",
+              "dram_bytes_per_launch": 57878603008 + 993063680,
+              "per_rk4_step": {"warp_inst": 111.280, "fp64_lane_slots": 65.335},
+              "pct": {"fp64_pipe": 55.80, "issue_active": 47.52, "lanes_per_inst": 19.18, "dram_throughput": 2.45}}
 SMS, SCHEDULERS_PER_SM = 152, 4
 
 
