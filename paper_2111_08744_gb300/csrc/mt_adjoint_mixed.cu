@@ -69,24 +69,33 @@ __device__ __noinline__ void acc_flush(const DevField& F, const RecBarM& R, cons
 
 // Add the cotangents (gbar, pebar) of the stage's interpolated grad phi and phi_eta to its CIC
 // records: g = v_s + wt (v_{s+1} - v_s), phi_eta = (phi_{s+1} - phi_s) ids, each corner with weight
-// prod (f or 1 - f).
-__device__ void acc_add(const DevField& F, const RecBarM& R, const ScatterAcc& sc, const StageF& sf,
-                        const float* gbar, float pebar, unsigned* err) {
+// prod (f or 1 - f); and, in the same pass over the corners, their pull-back to the stage position,
+// tb[d] += sum_c (d weight_c / dx_d) (a0 . r_c,s + a1 . r_c,s+1) with the stage's records r from the
+// lane cache (which holds the neighbourhood the stage interpolated from) and a0, a1 the cotangents
+// of the two slices' records.
+__device__ void acc_add(const DevField& F, const RecBarM& R, const ScatterAcc& sc, const LaneCache& lc,
+                        const StageF& sf, const float* gbar, float pebar, float* tb, unsigned* err) {
   const int4 key = make_int4((sf.lev << 8) | sf.sl, sf.i0[0], sf.i0[1], sf.i0[2]);
   const int4 old = *sc.key;
+  bool scatter = true;
   if (!(old.x == key.x && old.y == key.y && old.z == key.z && old.w == key.w)) {
     acc_flush(F, R, sc);
     if (sf.rows_ok) {  // the stage staged this neighbourhood and looked its rows up already
 #pragma unroll
       for (int c = 0; c < 8; ++c) sc.rows[c * sc.stride] = sf.rows[c];
+      *sc.key = key;
     } else {
       const long long i0l[3] = {sf.i0[0], sf.i0[1], sf.i0[2]};
       unsigned rows[8];
-      if (!cic_rows_compact(F, sf.lev, i0l, rows, err)) return;  // the stage interpolated from these 8 cells
+      // the stage interpolated from these 8 cells, so they exist; should the lookup fail all the same,
+      // the record cotangents are dropped (the accumulator stays empty) and the position part kept
+      scatter = cic_rows_compact(F, sf.lev, i0l, rows, err);
+      if (scatter) {
 #pragma unroll
-      for (int c = 0; c < 8; ++c) sc.rows[c * sc.stride] = rows[c];
+        for (int c = 0; c < 8; ++c) sc.rows[c * sc.stride] = rows[c];
+        *sc.key = key;
+      }
     }
-    *sc.key = key;
   }
   float a0[4], a1[4];
   if (F.S == 1) {
@@ -106,23 +115,38 @@ __device__ void acc_add(const DevField& F, const RecBarM& R, const ScatterAcc& s
       a1[1 + i] = sf.wt * gbar[i];
     }
   }
+  float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f;
 #pragma unroll 1
   for (int c = 0; c < 8; ++c) {
     const float wx = (c & 1) ? sf.f[0] : 1.0f - sf.f[0];
     const float wy = (c & 2) ? sf.f[1] : 1.0f - sf.f[1];
     const float wz = (c & 4) ? sf.f[2] : 1.0f - sf.f[2];
     const float w = wx * wy * wz;
+    const float4 r0 = lc.rec[(2 * c) * lc.stride];
+    const float4 r1 = lc.rec[(2 * c + 1) * lc.stride];
+    const float ar = a0[0] * r0.x + a0[1] * r0.y + a0[2] * r0.z + a0[3] * r0.w + a1[0] * r1.x + a1[1] * r1.y +
+                     a1[2] * r1.z + a1[3] * r1.w;
+    p0 += ((c & 1) ? 1.0f : -1.0f) * wy * wz * ar;
+    p1 += ((c & 2) ? 1.0f : -1.0f) * wx * wz * ar;
+    p2 += ((c & 4) ? 1.0f : -1.0f) * wx * wy * ar;
+    if (scatter) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      sc.acc[(8 * c + q) * sc.stride] += w * a0[q];
-      sc.acc[(8 * c + 4 + q) * sc.stride] += w * a1[q];
+      for (int q = 0; q < 4; ++q) {
+        sc.acc[(8 * c + q) * sc.stride] += w * a0[q];
+        sc.acc[(8 * c + 4 + q) * sc.stride] += w * a1[q];
+      }
     }
   }
+  const float inv = F.inv_dxf_f / (float)(1 << (F.L - sf.lev));  // d (level cell coordinate) / d x
+  tb[0] += p0 * inv;
+  tb[1] += p1 * inv;
+  tb[2] += p2 * inv;
 }
 
 // Transposed Jacobian of the FP32 right-hand side at a stage (Eqs. 2-4 with Eq. 4's D = grad phi . k
 // + phi_eta k0): tb = J^T w for the stage state (x[3], eta, k0, k[3]) and the cotangents of the
 // interpolated grad phi and phi_eta.  w: cotangents of K = (k[3], k0, dk0/dlambda, dk/dlambda).
+// The terms of tb[0..2] that go through the interpolant's spatial derivative are left to acc_add.
 __device__ __forceinline__ void stage_adjoint_mixed(const StageF& sf, float k0, const float* k, const float* w,
                                                     float* tb, float* gbar, float* pebar) {
   const float H = sf.H, pe = sf.pe, D = sf.D;
@@ -154,14 +178,10 @@ __device__ __forceinline__ void stage_adjoint_mixed(const StageF& sf, float k0, 
   tb[4] += pe * dDbar;
   tb[3] += sf.dH * dHbar;
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    tb[d] += sf.dpe[d] * dpebar;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) tb[d] += sf.G[i][d] * gbar[i];
-  }
-#pragma unroll
   for (int i = 0; i < 3; ++i) tb[3] += sf.ge[i] * gbar[i];
   *pebar = dpebar;
+  // the position part, sum_i gbar_i d g_i / dx_d + pebar d phi_eta / dx_d, is added by acc_add from the
+  // stage's records (the derivative of the interpolant applied to the cotangents directly)
 }
 
 // Reverse of one mixed step from the step-start state y (FP64 x[3], eta, k0, k[3]) and the step's
@@ -233,7 +253,7 @@ __device__ bool reverse_step_mixed(const DevField& F, const TraceArgs& A, const 
       return false;
     float gbar[3], pebar;
     stage_adjoint_mixed(sf, k0v, kv, Kb, tbn, gbar, &pebar);
-    if (Grav) acc_add(F, R, sc, sf, gbar, pebar, err);
+    if (Grav) acc_add(F, R, sc, *lc, sf, gbar, pebar, tbn, err);
 #pragma unroll
     for (int i = 0; i < 8; ++i) acc[i] += tbn[i];
     if (st > 0) {
