@@ -8,18 +8,19 @@
 //      a lane whose ray ends takes the next id of its warp's chunk), keeping the FP64 state every
 //      `checkpoint_every` steps, and write the ray's outputs;
 //   2. form the cotangent of the final state from dL/dxi, xi = x - (k/k0)(eta - eta_stop);
-//   3. (adjoint_mixed_kernel: a warp takes 32 consecutive ray ids at a time and runs their phases in
-//      lockstep) for each segment, last to first: recompute its steps from the checkpoint, keeping each step's
-//      start state and stage data (the stage wave-vector offsets, right-hand sides and step size),
-//      then reverse each step: the stages from the last to the first are evaluated again with the
-//      derivatives of the CIC interpolant (FP32) and their transposed Jacobians applied in FP32 to
-//      the stage cotangents, while the state's cotangent accumulates in FP64.  The parts of the step that are linear in
-//      the step-start state (x += h k, eta += h k0, and the step size's dependence on k0 and eta)
-//      are applied in FP64, as in the forward step;
+//   3. (adjoint_mixed_kernel: a warp takes 32 consecutive ray ids at a time and runs their phases
+//      in lockstep) for each segment, last to first: recompute its steps from the checkpoint,
+//      keeping each step's start state and stage data (the stage wave-vector offsets, right-hand
+//      sides and step size), then reverse each step: the stages from the last to the first are
+//      interpolated again (FP32) and their transposed Jacobians applied in FP32 to the stage
+//      cotangents, while the state's cotangent accumulates in FP64.  The parts of the step that are
+//      linear in the step-start state (x += h k, eta += h k0, and the step size's dependence on k0
+//      and eta) are applied in FP64, as in the forward step;
 //   4. the cotangents of grad phi and phi_eta at each stage go to the stage's 8 CIC records of both
 //      bracketing slices through a per-lane FP32 accumulator in shared memory, flushed with FP64
-//      atomics when the neighbourhood changes; phi at the observer (the initial wave vector)
-//      scatters once per ray.
+//      atomics when the neighbourhood changes; the same pass over the 8 corners pulls them back to
+//      the stage position through the derivative of the CIC weights; phi at the observer (the
+//      initial wave vector) scatters once per ray.
 // Rays that do not end with MT_RAY_OK contribute nothing.
 #include <cuda_runtime.h>
 
@@ -441,11 +442,11 @@ __global__ void __launch_bounds__(kAdjMBlock, 4) checkpoint_mixed_kernel(DevFiel
   }
 }
 
-// The mixed step, out of line: the forward pass and the segment recompute of the reverse sweep share
-// one copy of its code (inlined copies beside the reverse step outgrow the instruction cache); the
-// recompute records each step's stage data for the reverse step (rec null: no record).
-__device__ __forceinline__ bool step_out_of_line(const DevField& F, const TraceArgs& A, RayState& r, unsigned* err,
-                                              const LaneCache* lc, float* rec) {
+// The mixed step of the segment recompute: its CIC in the compact form (the sweep's code must fit
+// the instruction cache beside the reverse step), recording the step's stage data for the reverse
+// step in rec.
+__device__ __forceinline__ bool segment_step(const DevField& F, const TraceArgs& A, RayState& r, unsigned* err,
+                                          const LaneCache* lc, float* rec) {
   return ray_step_mixed<MT_INTERP_CIC, true, true>(F, A, r, err, lc, rec);
 }
 
@@ -568,7 +569,7 @@ __global__ void __launch_bounds__(kAdjMBlock, 3) adjoint_mixed_kernel(DevField F
       for (int st = 0; st < seg_len; ++st) {
         if (st < len) {
           for (int i = 0; i < 8; ++i) ys[st][i] = q.y[i];
-          step_out_of_line(F, A, q, err, &lc, rs[st]);  // the last step's end state is not kept
+          segment_step(F, A, q, err, &lc, rs[st]);  // the last step's end state is not kept
         }
         __syncwarp();
       }

@@ -134,6 +134,8 @@ __device__ __forceinline__ int tsc_first_level(const DevField& F, int l, const i
 // to the level-l cell coordinate d (the weights' derivatives, +-1 times the other two weights).
 // i0_out, f_out (if non-null) receive the lower corner and the in-cell fractions of the neighbourhood.
 // A neighbourhood found incomplete (false) is remembered in lc.neg when the lane has one.
+// rows_out, rows_ok (if non-null): when this call staged the neighbourhood, the rows of its 8 cells
+// and true (a call that reuses the staged neighbourhood leaves them as they were).
 // Compact: the miss path looks the rows up out of line and the corner loop stays rolled (the same
 // arithmetic in fewer instructions, for kernels whose hot loop outgrows the instruction cache).
 template <bool WithD = false, bool Compact = false>
@@ -601,8 +603,8 @@ __device__ bool ray_step_mixed(const DevField& F, const TraceArgsT& A, RayStateT
     const float kst[3] = {ks[0] + offk[0], ks[1] + offk[1], ks[2] + offk[2]};
     float Kk0, Kk[3], KI, Ks;
     int lf = 0;
-    if (!rhs_mixed<false, IP, Compact>(F, grav, B, eta, offx, offe, kst0, kst, &Kk0, Kk, &KI, &Ks, st == 0 ? &lf : nullptr, err,
-                              lc)) {
+    if (!rhs_mixed<false, IP, Compact>(F, grav, B, eta, offx, offe, kst0, kst, &Kk0, Kk, &KI, &Ks,
+                                       st == 0 ? &lf : nullptr, err, lc)) {
       r.status = MT_RAY_LEFT_DOMAIN;
       return true;
     }
