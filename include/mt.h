@@ -220,16 +220,19 @@ mt_status mt_trace_rays(const mt_octree* tree, const mt_trace_params* params, co
  * exact adjoint of the discrete map (RK4 stages, CIC weights, time slices, step-size and
  * last-step dependence, and phi at the observer).  States are checkpointed every
  * checkpoint_every (1..64) steps and each segment is recomputed.  Synchronous: the call
- * counts each ray's steps, allocates a temporary checkpoint buffer (8 doubles per
- * checkpoint), runs the sweep and frees it.  Rays that do not end with MT_RAY_OK add nothing.
+ * counts each ray's steps, allocates temporary buffers (the checkpoints, 8 doubles each; the
+ * step counts; on FP32 octrees also 9 doubles per ray that the forward pass leaves for the
+ * sweep), runs the forward pass and the sweep and frees them.  Rays that do not end with
+ * MT_RAY_OK add nothing.
  *
  * Both modes integrate each ray as mt_trace_rays does and differentiate that map: FP64
  * arithmetic on an FP64 octree; on an FP32 octree the mixed step (FP32 stages, FP64 state) with
  * FP32 stage derivatives and an FP64 tangent / cotangent state (reverse mode: per-lane FP32
  * accumulation of the record cotangents, added to dL_drec with FP64 atomics).  Reverse mode
  * supports MT_INTERP_CIC only (others: MT_ERR_UNSUPPORTED).  Both write the ray outputs `out`
- * (NULL pointers skip an output) of their integration.  A smaller checkpoint_every recomputes
- * less (1: every state is kept) at 8 doubles per checkpoint.
+ * (NULL pointers skip an output) of their integration.  checkpoint_every sets the checkpoint
+ * memory (8 doubles per checkpoint) and the length of the segments the sweep holds at a time;
+ * every step is integrated once more in the sweep whatever its value.
  * Errors: as mt_trace_rays; MT_ERR_INVALID_ARG if neither mode is requested or reverse-mode
  * arguments are incomplete; MT_ERR_OOM if the checkpoint buffer cannot be allocated.
  */
