@@ -93,3 +93,28 @@ def test_binding_fails_loudly_without_cuda():
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError):
         B.alloc_outputs(4)
+
+
+def _declared_arity():
+    """Number of parameters of every function prototype in mt.h."""
+    txt = open(os.path.join(ROOT, "include", "mt.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    txt = re.sub(r"//[^\n]*", "", txt)
+    out = {}
+    for m in re.finditer(r"\b(mt_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", txt):
+        params = " ".join(m.group(2).split())
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_marshals_every_entry_point_with_the_header_arity():
+    """The Python binding declares, for every mt.h entry point, as many ctypes arguments as the
+    prototype has parameters (the binding is argument marshalling only; a drift would pass garbage
+    through the C ABI)."""
+    lib = B.load()
+    arity = _declared_arity()
+    assert set(arity) == set(_declared_symbols())
+    for name, n in arity.items():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, f"{name}: no argtypes in the binding"
+        assert len(fn.argtypes) == n, f"{name}: binding has {len(fn.argtypes)} arguments, mt.h declares {n}"
